@@ -57,7 +57,7 @@ def lib():
             L.orc_integrate.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp]
             L.orc_extract.argtypes = [vp, vp, vp, vp]
             L.orc_block_set.restype = i64
-            L.orc_block_set.argtypes = [vp, vp, vp, i32, f32, f32, f32, f32, vp, i64]
+            L.orc_block_set.argtypes = [vp, vp, vp, i32, f32, f32, f32, f32, vp, vp, i64]
             L.orc_sampled.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, i32, i32, i32, f32, f32,
                                       vp, vp, i64, vp, vp, vp]
             L.orc_round_half.argtypes = [vp, i64, vp]
@@ -151,14 +151,15 @@ def _scan_arrays(scans: Sequence[np.ndarray], poses: Sequence[np.ndarray]):
     return pts, ptrs, counts, P
 
 
-def block_set(scans, poses, vs, trunc, min_range=0.1, max_range=1e9) -> np.ndarray:
+def block_set(scans, poses, vs, trunc, min_range=0.1, max_range=1e9, sensors=None) -> np.ndarray:
     """Sorted int32 [nb,3] keys of every block the scans' bands touch."""
     pts, ptrs, counts, P = _scan_arrays(scans, poses)
+    sens = np.ascontiguousarray(sensors if sensors is not None else np.zeros(len(pts)), dtype=np.int32)
     n = lib().orc_block_set(ptrs, _p(counts), _p(P), len(pts), vs, trunc, min_range, max_range,
-                            None, 0)
+                            _p(sens), None, 0)
     keys = np.zeros((max(n, 1), 3), dtype=np.int32)
     lib().orc_block_set(ptrs, _p(counts), _p(P), len(pts), vs, trunc, min_range, max_range,
-                        _p(keys), n)
+                        _p(sens), _p(keys), n)
     return keys[:n]
 
 

@@ -71,8 +71,11 @@ struct Ray {
 };
 
 // p = R ps + t, each row summed left to right; r = p - o with o = t.
-bool make_ray(const float* ps, const float* T, float min_range, float max_range, Ray* ray) {
+// A pinhole depth sensor only returns points in front of it (z > 0).
+bool make_ray(const float* ps, const float* T, float min_range, float max_range, int sensor,
+              Ray* ray) {
   if (!(std::isfinite(ps[0]) && std::isfinite(ps[1]) && std::isfinite(ps[2]))) return false;
+  if (sensor == 0 && !(ps[2] > 0.0f)) return false;
   for (int k = 0; k < 3; ++k) {
     float a = T[4 * k + 0] * ps[0];
     float b = T[4 * k + 1] * ps[1];
@@ -271,7 +274,7 @@ int orc_point_obs(const float* ps, const float* T, float vs, float trunc, float 
                   float max_range, int weight_mode, int dropoff, int sensor, float point_weight,
                   int32_t* vox, double* d, double* w, int cap, float* seg) {
   Ray ray;
-  if (!make_ray(ps, T, min_range, max_range, &ray)) return 0;
+  if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) return 0;
   float A[3], B[3];
   if (!band_segment(ray, trunc, vs, A, B)) return -2;
   if (seg) {
@@ -306,7 +309,7 @@ int orc_integrate(void* h, const float* pts, int64_t n, const float* T, const fl
   for (int64_t i = 0; i < n; ++i) {
     const float* ps = pts + 3 * i;
     Ray ray;
-    if (!make_ray(ps, T, min_range, max_range, &ray)) continue;
+    if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) continue;
     float A[3], B[3];
     if (!band_segment(ray, m->trunc, m->vs, A, B)) {
       ++bad;
@@ -373,13 +376,15 @@ void orc_extract(void* h, int32_t* keys, double* D, double* W) {
  * number of distinct blocks. */
 int64_t orc_block_set(const float* const* scans, const int64_t* counts, const float* poses,
                       int nscans, float vs, float trunc, float min_range, float max_range,
-                      int32_t* keys_out, int64_t cap) {
+                      const int* sensors, int32_t* keys_out, int64_t cap) {
   std::unordered_set<Key, KeyHash> blocks;
   std::vector<Key> vox;
   for (int s = 0; s < nscans; ++s) {
     for (int64_t i = 0; i < counts[s]; ++i) {
       Ray ray;
-      if (!make_ray(scans[s] + 3 * i, poses + 12 * s, min_range, max_range, &ray)) continue;
+      if (!make_ray(scans[s] + 3 * i, poses + 12 * s, min_range, max_range,
+                    sensors ? sensors[s] : 0, &ray))
+        continue;
       float A[3], B[3];
       if (!band_segment(ray, trunc, vs, A, B)) continue;
       vox.clear();
@@ -428,7 +433,8 @@ void orc_sampled(const float* const* scans, const int64_t* counts, const float* 
     for (int64_t i = 0; i < counts[s]; ++i) {
       const float* ps = scans[s] + 3 * i;
       Ray ray;
-      if (!make_ray(ps, poses + 12 * s, min_range, max_range, &ray)) continue;
+      if (!make_ray(ps, poses + 12 * s, min_range, max_range, sensors ? sensors[s] : 0, &ray))
+        continue;
       float A[3], B[3];
       if (!band_segment(ray, trunc, vs, A, B)) continue;
       vv.clear();

@@ -161,7 +161,7 @@ def test_distance_closed_form_oblique():
         T[[0, 5, 10]] = 1
         T[[3, 7, 11]] = o
         ps = (u * R).astype(np.float32)
-        res = orc.point_obs(ps, T, vs, tr)
+        res = orc.point_obs(ps, T, vs, tr, sensor=1)
         vox, d, w, seg = res
         # the integrator transforms in FP32: with R = I, p = ps + t rounded once
         p = (ps + T[[3, 7, 11]]).astype(np.float64)
