@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""TSDF integration throughput on GB300 (points/s, voxel-updates/s, SDF RMSE).
+
+Default workload: plain FP32 integration of 200 pinhole frames of 640x480
+(307,200 points each) on a random walk through a 30 x 30 x 5 m multi-room
+building (axial noise 0.0012 z^2, 2% dropout, voxel 0.05 m, trunc 0.15 m,
+quadratic weight with linear behind-surface drop-off), beside the same
+workload with FP16 storage.  One step = clear the submap + integrate all 200
+frames, replayed from a CUDA graph; inputs (737 MB of points) are resident in
+HBM and exceed L2.  `--workload lidar` runs the LiDAR/MAV workload through
+the batched path instead.
+
+`--impl reference` times the CPU oracle (FP64, single thread) on a bounded
+sample of the same workload: the only other place this file runs oracle code.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+# ---------------------------------------------------------------- helpers
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# -------------------------------------------------------------- workloads
+def make_workload(name: str, frames: int):
+    import scenegen as sg
+    if name == "multiroom":
+        return sg.make_c2(n_frames=frames)
+    if name == "room":
+        return sg.make_c1()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def sdf_rmse(scene, keys, D, W, vs, trunc):
+    """RMSE of stored D against the analytic scene distance (clamped to +-trunc)
+    over voxels with W > 0 and |D| < trunc."""
+    b, l = np.nonzero((W > 0) & (np.abs(D) < trunc))
+    if len(b) == 0:
+        return None
+    v = keys[b].astype(np.int64) * 8 + np.stack([l % 8, (l // 8) % 8, l // 64], 1)
+    c = (v + 0.5) * np.float64(np.float32(vs))
+    sdf = scene.sdf(c, trunc)
+    return float(np.sqrt(np.mean((D[b, l] - sdf) ** 2)))
+
+
+# -------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import _capi
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    peaks, peak_src = load_peaks()
+
+    wl = make_workload(args.workload, args.frames)
+    sm = wl.submaps[0]
+    F = len(sm.scans)
+    N = sm.scans[0].points.shape[0]
+    host = torch.from_numpy(np.stack([s.points for s in sm.scans])).pin_memory()
+    pts = host.cuda()
+    Ts = [s.T_sub_sensor for s in sm.scans]
+    params = cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range,
+                                  sm.scans[0].sensor, sm.scans[0].height, sm.scans[0].width,
+                                  args.ppc)
+    stream = torch.cuda.Stream()
+    max_blocks = args.max_blocks
+
+    def make_sub(storage):
+        with torch.cuda.stream(stream):
+            s = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
+                           stream=stream)
+        return s
+
+    def step(sub):
+        sub.reset(stream)
+        for f in range(F):
+            sub.integrate(pts[f], Ts[f], params, None, stream)
+
+    def capture(sub):
+        for _ in range(2):      # warm up the allocator and the kernels outside capture
+            step(sub)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            step(sub)
+        torch.cuda.synchronize()
+        return g
+
+    def timed(g, steps, warm):
+        for _ in range(warm):
+            g.replay()
+        barrier(ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        launches0 = _capi.cvx_launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+        barrier(ws)
+        return e0.elapsed_time(e1), _capi.cvx_launch_count() - launches0
+
+    sub32 = make_sub(cvx.CVX_STORE_F32)
+    g32 = capture(sub32)
+    # counters of exactly one step (reset clears them)
+    step(sub32)
+    torch.cuda.synchronize()
+    c1 = sub32.counters()
+    keys, D, W = (t.cpu().numpy() for t in sub32.extract(stream))
+    rmse32 = sdf_rmse(wl.scene, keys, D.astype(np.float64), W.astype(np.float64), sm.voxel_size, sm.trunc)
+    assert sub32.status() == 0, "device error during the benchmark workload"
+
+    clocks = Clocks(dev_index)
+    clocks.start()
+    ms32, graph_launches = timed(g32, args.steps, args.warmup)
+    clk = clocks.stop()
+    ms32 = max_over_ranks(ms32, ws)
+    # kernel launches inside the timed region: graph replays launch the
+    # captured kernels; count them from one captured step
+    per_step_launches = 1 + 3 * F
+
+    # per-kernel durations: profiled eager pass over the same steps
+    _capi.cvx_profile_start(1 << 22)
+    for _ in range(args.steps):
+        step(sub32)
+    torch.cuda.synchronize()
+    _capi.cvx_profile_stop()
+    prof = _capi.cvx_profile_read()
+
+    # FP16 storage form
+    sub16 = make_sub(cvx.CVX_STORE_F16)
+    g16 = capture(sub16)
+    step(sub16)
+    torch.cuda.synchronize()
+    keys16, D16, W16 = (t.cpu().numpy() for t in sub16.extract(stream))
+    D16 = D16.astype(np.float64) * np.float64(np.float32(sm.trunc))
+    rmse16 = sdf_rmse(wl.scene, keys16, D16, W16.astype(np.float64), sm.voxel_size, sm.trunc)
+    ms16, _ = timed(g16, args.steps, args.warmup)
+    ms16 = max_over_ranks(ms16, ws)
+    _capi.cvx_profile_start(1 << 22)
+    for _ in range(args.steps):
+        step(sub16)
+    torch.cuda.synchronize()
+    _capi.cvx_profile_stop()
+    prof16 = _capi.cvx_profile_read()
+
+    # end to end: pinned host points copied in on a side stream (double
+    # buffered), integrated through the public API, counters read back
+    copy_stream = torch.cuda.Stream()
+    bufs = [torch.empty((N, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    ev_copied = [torch.cuda.Event() for _ in range(2)]
+    ev_used = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_step():
+        sub32.reset(stream)
+        for f in range(F):
+            b = f & 1
+            copy_stream.wait_event(ev_used[b])
+            with torch.cuda.stream(copy_stream):
+                bufs[b].copy_(host[f], non_blocking=True)
+                ev_copied[b].record(copy_stream)
+            stream.wait_event(ev_copied[b])
+            sub32.integrate(bufs[b], Ts[f], params, None, stream)
+            ev_used[b].record(stream)
+        return sub32.counters()   # device -> host read of the step's result
+
+    for b in range(2):
+        ev_used[b].record(stream)
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier(ws)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws)
+
+    valid = c1["valid_points"]
+    obs = c1["observations"]
+    merged = c1["voxels_merged"]
+    blocks = c1["blocks_touched"]
+    new_blocks = c1["n_blocks"]
+    tot_valid = sum_over_ranks(valid, ws)
+    tot_obs = sum_over_ranks(obs, ws)
+    sec32 = ms32 / 1e3 / args.steps
+    sec16 = ms16 / 1e3 / args.steps
+    pts_s = tot_valid / sec32
+
+    # roofline of the dominant kernel (algorithmic bytes per launch / event time)
+    S32 = 8
+    bytes_kernel = {
+        "alloc_kernel": (12 * F * N + 16 * blocks + 12 * new_blocks) / F,
+        "accum_kernel": 12 * F * N / F,
+        "merge_kernel": 2 * S32 * merged / F,
+    }
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / prof[dom][1]
+    dom_bytes = bytes_kernel.get(dom, 0.0)
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    path_bytes = 12 * F * N + 2 * S32 * merged + 16 * blocks + S32 * 512 * new_blocks
+    path_gbs = path_bytes / sec32 / 1e9
+
+    out = {
+        "metric": "TSDF integration points/s (plain FP32, 1 GB300)",
+        "value": pts_s,
+        "unit": "points/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms32 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "frames_per_step": F, "points_per_frame": N,
+                   "voxel_size_m": sm.voxel_size, "trunc_m": sm.trunc, "weight": "quadratic+linear-dropoff",
+                   "storage": "f32", "step": "clear submap + integrate all frames (CUDA graph replay)",
+                   "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (F * N * 12 / 1e6),
+                   "parallelism": f"replica x{ws} (one submap sequence per GPU)"},
+        "voxel_updates_per_s": tot_obs / sec32,
+        "unique_voxel_merges_per_s": sum_over_ranks(merged, ws) / sec32,
+        "sdf_rmse_m": rmse32,
+        "counts_per_step": {"valid_points": valid, "observations": obs, "voxels_merged": merged,
+                            "blocks_touched": blocks, "blocks_allocated": new_blocks},
+        "forms": {"fp16_storage": {"points_per_s": tot_valid / sec16, "ms_per_step": ms16 / args.steps,
+                                   "speedup_vs_fp32": sec32 / sec16, "sdf_rmse_m": rmse16,
+                                   "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof16.items() if v[1]}}},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms},
+        "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / hbm},
+        "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
+        "kernel_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items() if v[1]},
+        "e2e": {"value": tot_valid / (e2e_ms / 1e3 / args.steps), "unit": "points/s",
+                "h2d_bytes_per_step": int(F * N * 12), "d2h_bytes_per_step": 48},
+        "gpu_launches": per_step_launches * args.steps,
+        "gpu_launches_counted": graph_launches,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for s in (sub32, sub16):
+        s.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- oracle timings
+def cpu_baseline(wl, seconds: float):
+    """The CPU oracle as it stands (FP64, one thread) on the first frames of
+    the same workload: enough frames for about `seconds` of CPU time."""
+    import oracle as orc
+    sm = wl.submaps[0]
+    om = orc.OracleSubmap(sm.voxel_size, sm.trunc, wl.max_weight, bool(wl.storage))
+    t0 = time.perf_counter()
+    valid = obs = frames = 0
+    for sc in sm.scans:
+        st = om.integrate(sc.points, sc.T_sub_sensor, None, wl.weight_mode, wl.dropoff, wl.min_range,
+                          wl.max_range, sc.sensor)
+        valid += st["valid"]
+        obs += st["obs"]
+        frames += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": valid / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "voxel_updates_per_s": obs / dt,
+            "sample": f"first {frames} of {len(sm.scans)} frames of {wl.name} ({valid} valid points, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, args.frames)
+    per = max(2.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        cpu_baseline(wl, per)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(wl, per))
+    el = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    print(json.dumps({
+        "impl": "reference", "metric": "TSDF integration points/s (plain FP32, 1 GB300)", "value": v,
+        "unit": "points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "step": "bounded sample: first frames of the workload"},
+        "cpu_baseline": {"value": v, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": vals[-1]["sample"]},
+        "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="multiroom", choices=["multiroom", "room"])
+    ap.add_argument("--frames", type=int, default=200)
+    ap.add_argument("--ppc", type=int, default=0, help="points per CTA of the accumulation pass")
+    ap.add_argument("--max-blocks", type=int, default=1 << 18)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * covox.h -- C ABI of the GB300 TSDF integration library (libcovox.so).
+ *
+ * Projective TSDF integration of range scans into block-hashed voxel submaps,
+ * as coVoxSLAM describes it:
+ *   - submaps are sparse sets of dense 8^3-voxel blocks indexed by their
+ *     integer 3-D position through a GPU open-addressing hash table, voxel
+ *     fields stored as separate arrays (Sec. III-A data layout, Sec. III-B
+ *     hash table with "activate", Sec. III-C two-level representation);
+ *   - a scan is integrated by ray casting every point, updating the voxels the
+ *     ray crosses within the truncation band around the point (Sec. III-C,
+ *     ray-casting paragraph), in a count / allocate / process sequence whose
+ *     per-voxel sums are reduced before they are merged (Sec. III-D).
+ *
+ * Conventions shared by every entry point:
+ *   - All calls are asynchronous on the caller's CUDA stream (`stream`, a
+ *     cudaStream_t; NULL = legacy default stream) unless stated otherwise.
+ *   - Device pointers are borrowed: they must stay valid until the stream has
+ *     executed the call.  The library never frees caller memory.
+ *   - Invalid arguments are detected on the host and returned at once
+ *     (CVX_ERR_INVALID_ARG); nothing is launched then.
+ *   - Errors found on the device (hash table full, block pool exhausted,
+ *     per-scan block budget exceeded, key out of range) set a per-scan error
+ *     word: the voxel-update (merge) phase of that scan is skipped, so stored
+ *     distances and weights are unchanged, while blocks allocated by the scan
+ *     stay allocated with zero weight.  The error is also OR-ed into a sticky
+ *     word read by cvx_submap_status().
+ *   - A submap is not thread safe: calls on one submap must be serialised.
+ *   - Voxel (i,j,k) of a submap holds the cube [i,i+1) x [j,j+1) x [k,k+1)
+ *     times the voxel size; its block key is (i>>3, j>>3, k>>3) (arithmetic
+ *     shift, i.e. floor division) and its local index lx + 8 ly + 64 lz with
+ *     lx = i & 7 etc.  Keys must stay within [-2^20, 2^20) per axis.
+ */
+#ifndef COVOX_H
+#define COVOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CVX_OK = 0,
+  CVX_ERR_INVALID_ARG = -1,
+  CVX_ERR_OOM = -2,        /* an allocation of the submap failed */
+  CVX_ERR_CAPACITY = -3,   /* hash table, block pool or per-scan budget full */
+  CVX_ERR_KEY_RANGE = -4,  /* a band endpoint left the +-2^23 voxel index range */
+  CVX_ERR_TIMEOUT = -5,    /* a bounded wait inside a persistent launch gave up */
+  CVX_ERR_CUDA = -6        /* a CUDA runtime call failed */
+} cvx_status;
+
+typedef enum { CVX_STORE_F32 = 0, CVX_STORE_F16 = 1 } cvx_storage;
+
+/* Integration weight of one observation (Sec. III-C, weighting paragraph):
+ * constant 1, quadratic 1/z^2 (z = optical-axis depth for a pinhole sensor,
+ * range for a spherical one), or a caller-supplied value per point. */
+typedef enum { CVX_W_CONST = 0, CVX_W_QUADRATIC = 1, CVX_W_PER_POINT = 2 } cvx_weight_mode;
+
+/* Behind-surface drop-off: for signed distance d < -vs the weight is scaled by
+ * f = (trunc + d) / (trunc - vs) (LINEAR) or f^2 (QUADRATIC); f reaches 0 at
+ * d = -trunc.  Requires trunc > voxel_size. */
+typedef enum { CVX_DROP_NONE = 0, CVX_DROP_LINEAR = 1, CVX_DROP_QUADRATIC = 2 } cvx_dropoff;
+
+typedef enum { CVX_SENSOR_PINHOLE = 0, CVX_SENSOR_SPHERICAL = 1 } cvx_sensor;
+
+/* Device-memory allocator hooks.  alloc returns NULL on failure; free receives
+ * the pointer and the size it was allocated with.  Both may be NULL, in which
+ * case the library uses cudaMalloc / cudaFree. */
+typedef void* (*cvx_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*cvx_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct {
+  float voxel_size;      /* metres, > 0 */
+  float trunc;           /* truncation distance, metres, > 0 */
+  float max_weight;      /* cap on the stored weight, > 0 */
+  int32_t storage;       /* cvx_storage */
+  int64_t max_blocks;    /* block pool capacity (blocks of 512 voxels) */
+  int64_t hash_slots;    /* hash table slots, a power of two >= 2 * max_blocks advised */
+  int64_t max_touched;   /* per-scan budget of distinct blocks (0: min(max_blocks, 65536)) */
+  cvx_alloc_fn alloc;
+  cvx_free_fn free;
+  void* alloc_ctx;
+  void* stream;          /* stream used for the creation-time clears */
+} cvx_submap_params;
+
+typedef struct {
+  int32_t weight_mode;   /* cvx_weight_mode */
+  int32_t dropoff;       /* cvx_dropoff */
+  float min_range;       /* points with |p - o| outside [min_range, max_range] are skipped */
+  float max_range;
+  int32_t height, width; /* organised scan layout (0, 0 = unorganised) */
+  int32_t sensor;        /* cvx_sensor: defines z of the quadratic weight */
+  int32_t pts_per_cta;   /* tuning: points per CTA of the accumulation pass (0 = default) */
+} cvx_integrate_params;
+
+typedef struct {
+  int64_t n_blocks;         /* allocated blocks */
+  int64_t frames;           /* scans integrated */
+  int64_t valid_points;     /* points that passed the validity test */
+  int64_t observations;     /* (point, voxel) pairs of the band traversals */
+  int64_t voxels_merged;    /* per-scan unique voxels whose D/W were updated, summed */
+  int64_t blocks_touched;   /* per-scan distinct blocks, summed */
+} cvx_counters;
+
+typedef struct cvx_submap cvx_submap;
+
+/* Create an empty submap (hash table, block pool with D and W per voxel,
+ * per-scan scratch).  Synchronous.  *out receives the handle. */
+cvx_status cvx_create_submap(const cvx_submap_params* params, cvx_submap** out);
+
+/* Integrate one scan as one frame (Sec. III-C ray casting; Sec. III-D count,
+ * allocate, process).  points_xyz: device float32 [n,3], sensor frame, NaN or
+ * out-of-range points skipped.  T_sub_sensor: HOST float32[12], 3x4 row-major
+ * rigid transform submap <- sensor (its translation is the sensor origin).
+ * point_weights: device float32 [n] for CVX_W_PER_POINT, else NULL.
+ * For every valid point p with unit ray direction u from the origin o, each
+ * voxel v crossed by the segment [p - trunc u, p + trunc u] receives the
+ * observation d = clamp((p - c_v).u, -trunc, trunc) (c_v = voxel centre) with
+ * weight w; then, per voxel, D <- (D W + sum w d) / (W + sum w) and
+ * W <- min(W + sum w, max_weight) when W + sum w > 0. */
+cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t n,
+                              const float T_sub_sensor[12], const float* point_weights,
+                              const cvx_integrate_params* params, void* stream);
+
+/* Copy out the allocated blocks in allocation order.  Two-call convention:
+ * with keys == NULL only *n_out (the number of blocks) is written.  Otherwise
+ * min(n_blocks, capacity) blocks are copied: keys int32 [cap,3], dist and
+ * weight [cap,512] in the storage type (float32, or float16 with dist holding
+ * D / trunc).  Pointers may be device or host memory.  Synchronises `stream`. */
+cvx_status cvx_extract_blocks(cvx_submap* map, int64_t capacity, int32_t* keys, void* dist,
+                              void* weight, int64_t* n_out, void* stream);
+
+/* Clear all blocks and counters (asynchronous, no host synchronisation). */
+cvx_status cvx_reset_submap(cvx_submap* map, void* stream);
+
+/* Sticky device error word as a status (CVX_OK if no error).  Synchronises the
+ * stream of the last call on this submap. */
+cvx_status cvx_submap_status(cvx_submap* map);
+
+/* Cumulative counters (synchronises like cvx_submap_status). */
+cvx_status cvx_submap_counters(cvx_submap* map, cvx_counters* out);
+
+/* Free the submap and everything it allocated (synchronises its stream). */
+void cvx_destroy(cvx_submap* map);
+
+/* Library version string. */
+const char* cvx_version(void);
+
+/* ---- tracing: launch accounting and per-kernel timing ----
+ * Every kernel launch of the library is counted.  While profiling is on, an
+ * event pair is recorded on the launching stream around each launch (up to
+ * max_launches launches); cvx_profile_read() synchronises on those events and
+ * returns, per kernel kind, its name (32 chars each), total milliseconds and
+ * number of timed launches, then clears the records.  Not thread safe. */
+cvx_status cvx_profile_start(int64_t max_launches);
+cvx_status cvx_profile_stop(void);
+int32_t cvx_profile_read(int32_t max_kinds, char* names, double* total_ms, int64_t* launches);
+int64_t cvx_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COVOX_H */

@@ -1,0 +1,194 @@
+"""ctypes binding of libcovox.so (include/covox.h): argument marshalling only.
+
+Every function keeps the C name and forwards device pointers of torch tensors
+and the raw CUDA stream handle; all integration work runs in the library's
+CUDA kernels.  There is no CPU path: if the library is missing or CUDA is not
+available the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcovox.so")
+
+CVX_OK, CVX_ERR_INVALID_ARG, CVX_ERR_OOM, CVX_ERR_CAPACITY = 0, -1, -2, -3
+CVX_ERR_KEY_RANGE, CVX_ERR_TIMEOUT, CVX_ERR_CUDA = -4, -5, -6
+CVX_STORE_F32, CVX_STORE_F16 = 0, 1
+CVX_W_CONST, CVX_W_QUADRATIC, CVX_W_PER_POINT = 0, 1, 2
+CVX_DROP_NONE, CVX_DROP_LINEAR, CVX_DROP_QUADRATIC = 0, 1, 2
+CVX_SENSOR_PINHOLE, CVX_SENSOR_SPHERICAL = 0, 1
+
+STATUS_NAMES = {0: "CVX_OK", -1: "CVX_ERR_INVALID_ARG", -2: "CVX_ERR_OOM", -3: "CVX_ERR_CAPACITY",
+                -4: "CVX_ERR_KEY_RANGE", -5: "CVX_ERR_TIMEOUT", -6: "CVX_ERR_CUDA"}
+
+
+class CovoxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cvx_submap_params(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_float), ("trunc", ctypes.c_float),
+                ("max_weight", ctypes.c_float), ("storage", ctypes.c_int32),
+                ("max_blocks", ctypes.c_int64), ("hash_slots", ctypes.c_int64),
+                ("max_touched", ctypes.c_int64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+class cvx_integrate_params(ctypes.Structure):
+    _fields_ = [("weight_mode", ctypes.c_int32), ("dropoff", ctypes.c_int32),
+                ("min_range", ctypes.c_float), ("max_range", ctypes.c_float),
+                ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("sensor", ctypes.c_int32), ("pts_per_cta", ctypes.c_int32)]
+
+
+class cvx_counters(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int64), ("frames", ctypes.c_int64),
+                ("valid_points", ctypes.c_int64), ("observations", ctypes.c_int64),
+                ("voxels_merged", ctypes.c_int64), ("blocks_touched", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/covox.h
+_vp, _i64, _i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+SIGNATURES = {
+    "cvx_version": (ctypes.c_char_p, []),
+    "cvx_create_submap": (_i32, [ctypes.POINTER(cvx_submap_params), ctypes.POINTER(_vp)]),
+    "cvx_integrate_scan": (_i32, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(cvx_integrate_params), _vp]),
+    "cvx_extract_blocks": (_i32, [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64), _vp]),
+    "cvx_reset_submap": (_i32, [_vp, _vp]),
+    "cvx_submap_status": (_i32, [_vp]),
+    "cvx_submap_counters": (_i32, [_vp, ctypes.POINTER(cvx_counters)]),
+    "cvx_destroy": (None, [_vp]),
+    "cvx_profile_start": (_i32, [_i64]),
+    "cvx_profile_stop": (_i32, []),
+    "cvx_profile_read": (_i32, [_i32, _vp, _vp, _vp]),
+    "cvx_launch_count": (_i64, []),
+}
+
+
+def lib():
+    """Load libcovox.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "paper_2410_21149_gb300._build.build() (nvcc, sm_103a)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str) -> None:
+    if status != CVX_OK:
+        raise CovoxError(status, what)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_ptr(t, dtype_name: str, what: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if str(t.dtype) != dtype_name or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous {dtype_name} tensor")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------ entry points
+def cvx_version() -> str:
+    return lib().cvx_version().decode()
+
+
+def cvx_create_submap(params: cvx_submap_params) -> int:
+    h = ctypes.c_void_p()
+    check(lib().cvx_create_submap(ctypes.byref(params), ctypes.byref(h)), "cvx_create_submap")
+    return h.value
+
+
+def cvx_integrate_scan(handle: int, points, T_sub_sensor, point_weights, params: cvx_integrate_params,
+                       stream=None) -> None:
+    n = int(points.shape[0])
+    pp = _dev_ptr(points, "torch.float32", "points") if n else None
+    pw = None if point_weights is None else _dev_ptr(point_weights, "torch.float32", "point_weights")
+    T = np.ascontiguousarray(T_sub_sensor, dtype=np.float32).reshape(12)
+    check(lib().cvx_integrate_scan(handle, pp, n, T.ctypes.data_as(ctypes.c_void_p), pw,
+                                   ctypes.byref(params), _stream_handle(stream)), "cvx_integrate_scan")
+
+
+def cvx_extract_blocks(handle: int, capacity: int, keys, dist, weight, stream=None) -> int:
+    n = ctypes.c_int64(0)
+    ptr = (lambda t: None if t is None else t.data_ptr())
+    check(lib().cvx_extract_blocks(handle, capacity, ptr(keys), ptr(dist), ptr(weight), ctypes.byref(n),
+                                   _stream_handle(stream)), "cvx_extract_blocks")
+    return n.value
+
+
+def cvx_reset_submap(handle: int, stream=None) -> None:
+    check(lib().cvx_reset_submap(handle, _stream_handle(stream)), "cvx_reset_submap")
+
+
+def cvx_submap_status(handle: int) -> int:
+    return int(lib().cvx_submap_status(handle))
+
+
+def cvx_submap_counters(handle: int) -> dict:
+    c = cvx_counters()
+    check(lib().cvx_submap_counters(handle, ctypes.byref(c)), "cvx_submap_counters")
+    return {f: int(getattr(c, f)) for f, _ in cvx_counters._fields_}
+
+
+def cvx_destroy(handle: int) -> None:
+    if handle:
+        lib().cvx_destroy(handle)
+
+
+def cvx_profile_start(max_launches: int = 1 << 20) -> None:
+    check(lib().cvx_profile_start(max_launches), "cvx_profile_start")
+
+
+def cvx_profile_stop() -> None:
+    check(lib().cvx_profile_stop(), "cvx_profile_stop")
+
+
+def cvx_profile_read() -> dict:
+    """{kernel name: (total ms, timed launches)} since the last read (synchronises)."""
+    k = 16
+    names = ctypes.create_string_buffer(32 * k)
+    tot = np.zeros(k, np.float64)
+    cnt = np.zeros(k, np.int64)
+    n = lib().cvx_profile_read(k, names, tot.ctypes.data_as(ctypes.c_void_p),
+                               cnt.ctypes.data_as(ctypes.c_void_p))
+    raw = names.raw
+    out = {}
+    for q in range(n):
+        name = raw[32 * q:32 * q + 32].split(b"\0")[0].decode()
+        out[name] = (float(tot[q]), int(cnt[q]))
+    return out
+
+
+def cvx_launch_count() -> int:
+    return int(lib().cvx_launch_count())

@@ -1,0 +1,234 @@
+// covox_dev.cuh -- device-side building blocks of the integration path:
+// the block hash (coVoxSLAM Sec. III-B), the FP32 band traversal (Sec. III-C
+// ray casting, Amanatides-Woo), the observation distance/weight, and the
+// device views of a submap and of a scan.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace covox {
+
+constexpr int kVoxPerBlock = 512;           // 8^3
+constexpr uint64_t kEmptyKey = ~0ull;       // unreachable: packed keys use 63 bits
+constexpr float kKeyLimit = 8388608.0f;     // 2^23 voxels = 2^20 blocks per axis
+
+enum : int32_t { kErrCapacity = 1, kErrKeyRange = 2, kErrTimeout = 4 };
+
+// Device-resident bookkeeping of one submap.
+struct State {
+  int32_t n_blocks;     // block pool bump pointer (allocation phase, Sec. III-D)
+  int32_t n_touched;    // distinct blocks of the current scan
+  int32_t frame_err;    // error bits of the current scan
+  int32_t sticky_err;   // OR of all scans' error bits
+  uint32_t ticket;      // last-CTA detection of the merge pass
+  int32_t pad[3];
+  unsigned long long frames, valid_pts, obs, voxels_merged, blocks_touched;
+};
+
+// Everything a kernel needs to address one submap (passed by value).
+struct SubmapDev {
+  unsigned long long* keys;   // [slots] packed block keys, kEmptyKey when free
+  int32_t* vals;              // [slots] pool index of the slot's block (-1: none)
+  int32_t* touch;             // [slots] per-scan block slot j, -1 when untouched
+  int32_t* block_keys;        // [max_blocks,3] integer block coordinates
+  void* D;                    // [max_blocks,512] float or half (D / trunc)
+  void* W;                    // [max_blocks,512] float or half
+  float2* acc;                // [max_touched,512] per-scan sums (sum w d, sum w)
+  int32_t* touched;           // [max_touched] hash slot of each touched block
+  State* st;
+  uint32_t slot_mask;
+  int32_t max_probe;
+  int32_t max_blocks;
+  int32_t max_touched;
+  float vs, inv_vs, trunc, max_w;
+};
+
+// One scan (frame) as the kernels see it.
+struct ScanDev {
+  const float* pts;      // [n,3] sensor frame
+  const float* pw;       // [n] per-point weights or nullptr
+  long long n;
+  float T[12];           // submap <- sensor, row-major 3x4
+  float min_range, max_range;
+  int32_t weight_mode, dropoff, sensor, pad;
+};
+
+// ------------------------------------------------------------------ hash
+__device__ __forceinline__ unsigned long long pack_key(int bx, int by, int bz) {
+  return ((unsigned long long)(uint32_t)(bx + (1 << 20)) << 42) |
+         ((unsigned long long)(uint32_t)(by + (1 << 20)) << 21) |
+         (unsigned long long)(uint32_t)(bz + (1 << 20));
+}
+
+__device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return (uint32_t)k;
+}
+
+// Insert-or-find ("activate", Sec. III-B): returns the slot of `key`, or -1
+// if the bounded probe found no room.  *inserted tells whether this call
+// claimed the slot.
+__device__ __forceinline__ int hash_activate(const SubmapDev& m, unsigned long long key,
+                                             bool* inserted) {
+  uint32_t s = hash_key(key) & m.slot_mask;
+  *inserted = false;
+  for (int p = 0; p < m.max_probe; ++p) {
+    unsigned long long cur = *((volatile unsigned long long*)(m.keys + s));
+    if (cur == key) return (int)s;
+    if (cur == kEmptyKey) {
+      unsigned long long old = atomicCAS(m.keys + s, kEmptyKey, key);
+      if (old == kEmptyKey) {
+        *inserted = true;
+        return (int)s;
+      }
+      if (old == key) return (int)s;
+    }
+    s = (s + 1) & m.slot_mask;
+  }
+  return -1;
+}
+
+// Lookup only (keys are not modified by the caller's kernel).
+__device__ __forceinline__ int hash_find(const SubmapDev& m, unsigned long long key) {
+  uint32_t s = hash_key(key) & m.slot_mask;
+  for (int p = 0; p < m.max_probe; ++p) {
+    unsigned long long cur = __ldg(m.keys + s);
+    if (cur == key) return (int)s;
+    if (cur == kEmptyKey) return -1;
+    s = (s + 1) & m.slot_mask;
+  }
+  return -1;
+}
+
+// --------------------------------------------------------- ray and band
+// Point transform p = R ps + t (row sums left to right), r = p - o with
+// o = t, len = |r|, u = r / len.  FP32 with explicit round-to-nearest
+// intrinsics so that nothing is contracted into an FMA: the traversal below
+// must reproduce the same voxels bit for bit on any IEEE FP32 machine.
+struct Ray {
+  float p[3], o[3], u[3], len;
+};
+
+__device__ __forceinline__ bool make_ray(const ScanDev& sc, long long i, Ray& r) {
+  const float x = __ldg(sc.pts + 3 * i), y = __ldg(sc.pts + 3 * i + 1), z = __ldg(sc.pts + 3 * i + 2);
+  if (!(isfinite(x) && isfinite(y) && isfinite(z))) return false;
+  if (sc.sensor == 0 && !(z > 0.0f)) return false;   // a depth camera sees only z > 0
+  float rr[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s = __fadd_rn(__fmul_rn(sc.T[4 * k], x), __fmul_rn(sc.T[4 * k + 1], y));
+    s = __fadd_rn(s, __fmul_rn(sc.T[4 * k + 2], z));
+    r.p[k] = __fadd_rn(s, sc.T[4 * k + 3]);
+    r.o[k] = sc.T[4 * k + 3];
+    rr[k] = __fsub_rn(r.p[k], r.o[k]);
+  }
+  float l2 = __fmul_rn(rr[0], rr[0]);
+  l2 = __fadd_rn(l2, __fmul_rn(rr[1], rr[1]));
+  l2 = __fadd_rn(l2, __fmul_rn(rr[2], rr[2]));
+  r.len = __fsqrt_rn(l2);
+  if (!(r.len >= sc.min_range && r.len <= sc.max_range)) return false;
+  const float il = __frcp_rn(r.len);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.u[k] = __fmul_rn(rr[k], il);
+  return true;
+}
+
+// Band endpoints in voxel units: A = (p - trunc u) / vs, B = (p + trunc u) / vs
+// (the division is a multiply by the FP32 reciprocal of vs).  False if an
+// endpoint leaves the key range.
+__device__ __forceinline__ bool band(const Ray& r, float trunc, float inv_vs, float A[3], float B[3]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float tu = __fmul_rn(trunc, r.u[k]);
+    A[k] = __fmul_rn(__fsub_rn(r.p[k], tu), inv_vs);
+    B[k] = __fmul_rn(__fadd_rn(r.p[k], tu), inv_vs);
+    ok = ok && (A[k] >= -kKeyLimit) && (A[k] < kKeyLimit) && (B[k] >= -kKeyLimit) && (B[k] < kKeyLimit);
+  }
+  return ok;
+}
+
+// Amanatides-Woo traversal of A -> B.  The next axis is the one with the
+// smallest tMax among axes not yet at their end cell; ties take the lowest
+// axis.  tMax starts at the first boundary crossing times 1/|B - A| and grows
+// by that reciprocal per step.
+struct Dda {
+  int v[3], e[3], s[3];
+  float tm[3], td[3];
+  int left;
+
+  __device__ __forceinline__ void init(const float A[3], const float B[3]) {
+    left = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      v[k] = (int)floorf(A[k]);
+      e[k] = (int)floorf(B[k]);
+      const float d = __fsub_rn(B[k], A[k]);
+      if (d > 0.0f) {
+        s[k] = 1;
+        td[k] = __frcp_rn(d);
+        tm[k] = __fmul_rn(__fsub_rn((float)(v[k] + 1), A[k]), td[k]);
+      } else if (d < 0.0f) {
+        s[k] = -1;
+        td[k] = __frcp_rn(-d);
+        tm[k] = __fmul_rn(__fsub_rn(A[k], (float)v[k]), td[k]);
+      } else {
+        s[k] = 0;
+        td[k] = __int_as_float(0x7f800000);
+        tm[k] = __int_as_float(0x7f800000);
+      }
+      left += abs(e[k] - v[k]);
+    }
+  }
+
+  __device__ __forceinline__ void step() {
+    int best = -1;
+    float bt = 0.0f;
+    if (v[0] != e[0]) { best = 0; bt = tm[0]; }
+    if (v[1] != e[1] && (best < 0 || tm[1] < bt)) { best = 1; bt = tm[1]; }
+    if (v[2] != e[2] && (best < 0 || tm[2] < bt)) { best = 2; }
+    if (best == 0) { v[0] += s[0]; tm[0] = __fadd_rn(tm[0], td[0]); }
+    else if (best == 1) { v[1] += s[1]; tm[1] = __fadd_rn(tm[1], td[1]); }
+    else { v[2] += s[2]; tm[2] = __fadd_rn(tm[2], td[2]); }
+    --left;
+  }
+};
+
+// ---------------------------------------------------- distance and weight
+// d = (p - c_v).u with c_v = (v + 1/2) vs.  Each component p - (v+1/2) vs is
+// one FMA (v + 1/2 is exact for |v| < 2^23), so the residual carries a single
+// rounding however far the submap origin is.
+__device__ __forceinline__ float voxel_distance(const Ray& r, const int v[3], float vs, float trunc) {
+  const float q0 = fmaf(-((float)v[0] + 0.5f), vs, r.p[0]);
+  const float q1 = fmaf(-((float)v[1] + 0.5f), vs, r.p[1]);
+  const float q2 = fmaf(-((float)v[2] + 0.5f), vs, r.p[2]);
+  const float d = fmaf(q2, r.u[2], fmaf(q1, r.u[1], q0 * r.u[0]));
+  return fminf(fmaxf(d, -trunc), trunc);
+}
+
+__device__ __forceinline__ float base_weight(const ScanDev& sc, long long i, const Ray& r) {
+  if (sc.weight_mode == 0) return 1.0f;
+  if (sc.weight_mode == 2) return __ldg(sc.pw + i);
+  const float z = sc.sensor == 0 ? __ldg(sc.pts + 3 * i + 2) : r.len;
+  return 1.0f / (z * z);
+}
+
+__device__ __forceinline__ float dropoff_weight(float w, float d, float vs, float trunc, int mode) {
+  if (mode != 0 && d < -vs) {
+    float f = fmaxf((trunc + d) / (trunc - vs), 0.0f);
+    return mode == 1 ? w * f : w * f * f;
+  }
+  return w;
+}
+
+__device__ __forceinline__ int floor_div8(int v) { return v >> 3; }   // arithmetic shift
+__device__ __forceinline__ int local_index(const int v[3]) {
+  return (v[0] & 7) | ((v[1] & 7) << 3) | ((v[2] & 7) << 6);
+}
+
+}  // namespace covox

@@ -1,0 +1,91 @@
+"""Shared test harness: run a workload through the CUDA library and through
+the oracle, and compare the submaps element by element."""
+from __future__ import annotations
+
+import numpy as np
+
+import scenegen as sg
+
+
+def int_params(wl: sg.Workload, scan: sg.Scan, **over):
+    import paper_2410_21149_gb300 as cvx
+    kw = dict(weight_mode=wl.weight_mode, dropoff=wl.dropoff, min_range=wl.min_range,
+              max_range=wl.max_range, sensor=scan.sensor, height=scan.height, width=scan.width)
+    kw.update(over)
+    return cvx.integrate_params(**kw)
+
+
+def run_gpu(wl: sg.Workload, storage=None, max_blocks=1 << 17, point_weights=None, **over):
+    """Integrate every submap of the workload; returns a list of
+    (keys [nb,3] int32, D [nb,512] float64 metres, W [nb,512] float64, counters)."""
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    storage = wl.storage if storage is None else storage
+    out = []
+    for m, sm in enumerate(wl.submaps):
+        sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks)
+        for k, sc in enumerate(sm.scans):
+            pts = torch.from_numpy(np.ascontiguousarray(sc.points)).cuda()
+            pw = None
+            if point_weights is not None:
+                pw = torch.from_numpy(np.ascontiguousarray(point_weights[m][k], np.float32)).cuda()
+            sub.integrate(pts, sc.T_sub_sensor, int_params(wl, sc, **over), pw)
+        keys, D, W = sub.extract()
+        torch.cuda.synchronize()
+        keys = keys.cpu().numpy()
+        D = D.cpu().numpy().astype(np.float64)
+        W = W.cpu().numpy().astype(np.float64)
+        if storage == 1:
+            D = D * np.float64(np.float32(sm.trunc))
+        out.append((keys, D, W, sub.counters(), sub.status()))
+        sub.close()
+    return out
+
+
+def run_oracle(wl: sg.Workload, fp16=None, point_weights=None):
+    import oracle as orc
+    fp16 = bool(wl.storage) if fp16 is None else fp16
+    out = []
+    for m, sm in enumerate(wl.submaps):
+        om = orc.OracleSubmap(sm.voxel_size, sm.trunc, wl.max_weight, fp16)
+        tot = {}
+        for k, sc in enumerate(sm.scans):
+            pw = None if point_weights is None else point_weights[m][k]
+            st = om.integrate(sc.points, sc.T_sub_sensor, pw, wl.weight_mode, wl.dropoff,
+                              wl.min_range, wl.max_range, sc.sensor)
+            for key, v in st.items():
+                tot[key] = tot.get(key, 0) + v
+        keys, D, W = om.extract()
+        out.append((keys, D, W, tot))
+    return out
+
+
+def sort_blocks(keys, D, W):
+    order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+    return keys[order], D[order], W[order]
+
+
+def compare(gpu, orc, d_tol, w_rel=1e-4, w_floor=1e-6, fp16_trunc=None):
+    """Block sets bit-exact; W within w_rel relative (abs floor w_floor, or one
+    half ulp for FP16 storage); D within d_tol where both weights are above the
+    floor.  Returns a dict of the largest errors."""
+    kg, Dg, Wg, cnt, status = gpu
+    ko, Do, Wo, tot = orc
+    assert status == 0, status
+    kg, Dg, Wg = sort_blocks(kg, Dg, Wg)
+    assert kg.shape == ko.shape, (kg.shape, ko.shape)
+    assert np.array_equal(kg, ko), "block sets differ"
+    if fp16_trunc is None:
+        wtol = w_rel * np.abs(Wo) + w_floor
+    else:
+        ulp = np.exp2(np.floor(np.log2(np.maximum(np.abs(Wo), 2.0 ** -14))) - 10)
+        wtol = ulp + w_floor
+    werr = np.abs(Wg - Wo)
+    assert (werr <= wtol).all(), f"W error {werr.max()} (at W={Wo.flat[np.argmax(werr - wtol)]})"
+    both = (Wo > w_floor) & (Wg > w_floor)
+    same = ((Wo > 0) == (Wg > 0)) | (np.maximum(Wo, Wg) <= 10 * w_floor)
+    assert same.all(), "voxel sets with weight differ"
+    derr = np.abs(Dg - Do)[both]
+    assert derr.size == 0 or derr.max() <= d_tol, f"D error {derr.max()}"
+    return {"d_max": float(derr.max()) if derr.size else 0.0, "w_max": float(werr.max()),
+            "voxels": int(both.sum()), "blocks": int(len(ko))}
