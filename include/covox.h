@@ -20,7 +20,7 @@
  *   - Invalid arguments are detected on the host and returned at once
  *     (CVX_ERR_INVALID_ARG); nothing is launched then.
  *   - Errors found on the device (hash table full, block pool exhausted,
- *     per-scan block budget exceeded, key out of range) set a per-scan error
+ *     key out of range, a bounded wait that gave up) set a per-scan error
  *     word: the voxel-update (merge) phase of that scan is skipped, so stored
  *     distances and weights are unchanged, while blocks allocated by the scan
  *     stay allocated with zero weight.  The error is also OR-ed into a sticky
@@ -45,7 +45,7 @@ typedef enum {
   CVX_OK = 0,
   CVX_ERR_INVALID_ARG = -1,
   CVX_ERR_OOM = -2,        /* an allocation of the submap failed */
-  CVX_ERR_CAPACITY = -3,   /* hash table, block pool or per-scan budget full */
+  CVX_ERR_CAPACITY = -3,   /* hash table or block pool full */
   CVX_ERR_KEY_RANGE = -4,  /* a band endpoint left the +-2^23 voxel index range */
   CVX_ERR_TIMEOUT = -5,    /* a bounded wait inside a persistent launch gave up */
   CVX_ERR_CUDA = -6        /* a CUDA runtime call failed */
@@ -78,7 +78,7 @@ typedef struct {
   int32_t storage;       /* cvx_storage */
   int64_t max_blocks;    /* block pool capacity (blocks of 512 voxels) */
   int64_t hash_slots;    /* hash table slots, a power of two >= 2 * max_blocks advised */
-  int64_t max_touched;   /* per-scan budget of distinct blocks (0: min(max_blocks, 65536)) */
+  int64_t reserved;      /* must be 0 */
   cvx_alloc_fn alloc;
   cvx_free_fn free;
   void* alloc_ctx;
@@ -92,7 +92,11 @@ typedef struct {
   float max_range;
   int32_t height, width; /* organised scan layout (0, 0 = unorganised) */
   int32_t sensor;        /* cvx_sensor: defines z of the quadratic weight */
-  int32_t pts_per_cta;   /* tuning: points per CTA of the accumulation pass (0 = default) */
+  int32_t pts_per_cta;   /* tuning: points per CTA tile (0 = default; organised scans use
+                            32-pixel-wide tiles of pts_per_cta / 32 rows) */
+  int32_t local_blocks;  /* tuning: shared-memory block slots per CTA: 0 = default (8), else a
+                            power of two <= 32 */
+  int32_t reserved;      /* must be 0 */
 } cvx_integrate_params;
 
 typedef struct {

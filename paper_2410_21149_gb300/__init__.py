@@ -41,9 +41,10 @@ def _torch_allocator():
 
 def integrate_params(weight_mode=CVX_W_CONST, dropoff=CVX_DROP_NONE, min_range=0.1,
                      max_range=1e9, sensor=CVX_SENSOR_PINHOLE, height=0, width=0,
-                     pts_per_cta=0) -> cvx_integrate_params:
+                     pts_per_cta=0, local_blocks=0) -> cvx_integrate_params:
     return cvx_integrate_params(int(weight_mode), int(dropoff), float(min_range), float(max_range),
-                                int(height), int(width), int(sensor), int(pts_per_cta))
+                                int(height), int(width), int(sensor), int(pts_per_cta),
+                                int(local_blocks), 0)
 
 
 class Submap:
@@ -51,7 +52,7 @@ class Submap:
 
     def __init__(self, voxel_size: float, trunc: float, max_weight: float = 1e4,
                  storage: int = CVX_STORE_F32, max_blocks: int = 1 << 16,
-                 hash_slots: Optional[int] = None, max_touched: int = 0,
+                 hash_slots: Optional[int] = None,
                  use_torch_allocator: bool = True, stream=None):
         import torch
         if not torch.cuda.is_available():
@@ -60,7 +61,7 @@ class Submap:
             hash_slots = 1 << max(1, int(np.ceil(np.log2(2 * max_blocks))))
         self._fns = _torch_allocator() if use_torch_allocator else (_capi.ALLOC_FN(), _capi.FREE_FN())
         p = cvx_submap_params(float(voxel_size), float(trunc), float(max_weight), int(storage),
-                              int(max_blocks), int(hash_slots), int(max_touched),
+                              int(max_blocks), int(hash_slots), 0,
                               self._fns[0], self._fns[1], None, _capi._stream_handle(stream))
         self.voxel_size, self.trunc, self.max_weight, self.storage = voxel_size, trunc, max_weight, storage
         self.max_blocks, self.hash_slots = max_blocks, hash_slots

@@ -42,7 +42,7 @@ class cvx_submap_params(ctypes.Structure):
     _fields_ = [("voxel_size", ctypes.c_float), ("trunc", ctypes.c_float),
                 ("max_weight", ctypes.c_float), ("storage", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int64), ("hash_slots", ctypes.c_int64),
-                ("max_touched", ctypes.c_int64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("reserved", ctypes.c_int64), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
 
 
@@ -50,7 +50,8 @@ class cvx_integrate_params(ctypes.Structure):
     _fields_ = [("weight_mode", ctypes.c_int32), ("dropoff", ctypes.c_int32),
                 ("min_range", ctypes.c_float), ("max_range", ctypes.c_float),
                 ("height", ctypes.c_int32), ("width", ctypes.c_int32),
-                ("sensor", ctypes.c_int32), ("pts_per_cta", ctypes.c_int32)]
+                ("sensor", ctypes.c_int32), ("pts_per_cta", ctypes.c_int32),
+                ("local_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class cvx_counters(ctypes.Structure):

@@ -29,29 +29,33 @@ struct State {
 // Everything a kernel needs to address one submap (passed by value).
 struct SubmapDev {
   unsigned long long* keys;   // [slots] packed block keys, kEmptyKey when free
-  int32_t* vals;              // [slots] pool index of the slot's block (-1: none)
-  int32_t* touch;             // [slots] per-scan block slot j, -1 when untouched
+  int32_t* vals;              // [slots] pool index of the slot's block (-1: not yet published, -3: none)
+  int32_t* touch;             // [max_blocks] per-scan touched-list position, -1 when untouched
   int32_t* block_keys;        // [max_blocks,3] integer block coordinates
   void* D;                    // [max_blocks,512] float or half (D / trunc)
   void* W;                    // [max_blocks,512] float or half
-  float2* acc;                // [max_touched,512] per-scan sums (sum w d, sum w)
-  int32_t* touched;           // [max_touched] hash slot of each touched block
+  float2* acc;                // [max_blocks,512] per-scan sums (sum w d, sum w), zero between scans
+  int32_t* touched;           // [max_blocks] pool index of each block touched by the scan
   State* st;
   uint32_t slot_mask;
   int32_t max_probe;
   int32_t max_blocks;
   int32_t max_touched;
   float vs, inv_vs, trunc, max_w;
+  int32_t storage;
 };
 
-// One scan (frame) as the kernels see it.
+// One scan (frame) as the kernels see it, with its tiling: an organised
+// scan (height x width == n) is cut into tile_w x tile_h pixel tiles, an
+// unorganised one into runs of tile_w * tile_h consecutive points.
 struct ScanDev {
   const float* pts;      // [n,3] sensor frame
   const float* pw;       // [n] per-point weights or nullptr
   long long n;
   float T[12];           // submap <- sensor, row-major 3x4
   float min_range, max_range;
-  int32_t weight_mode, dropoff, sensor, pad;
+  int32_t weight_mode, dropoff, sensor, organised;
+  int32_t height, width, tile_w, tile_h, tiles_x, n_tiles;
 };
 
 // ------------------------------------------------------------------ hash

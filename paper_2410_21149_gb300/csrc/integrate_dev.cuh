@@ -1,0 +1,332 @@
+// integrate_dev.cuh -- the two phases of integrating one scan, as device
+// functions shared by the per-scan kernels and the persistent batched kernel.
+//
+//   integrate_tile : count + allocate + reduce for one tile of points
+//                    (coVoxSLAM Sec. III-D): one band traversal per point,
+//                    per-voxel sums of the tile's blocks in shared memory,
+//                    then one activation per distinct block (Sec. III-B) and a
+//                    vector-atomic flush into the blocks' per-scan sums.
+//   merge_block    : one touched block: D <- (D W + sum w d)/(W + sum w),
+//                    W <- min(W + sum w, max_weight) for voxels with sum w > 0,
+//                    with vectorised loads/stores; clears the accumulator.
+#pragma once
+
+#include "covox_dev.cuh"
+
+namespace covox {
+
+constexpr int kTileThreads = 256;
+constexpr int kTileBlocks = 64;      // distinct blocks recorded per tile (power of two)
+constexpr int kMapDead = -3;         // vals[] marker: block unusable (pool exhausted)
+constexpr long long kSpinLimit = 1 << 22;
+
+// Global activation of one block (insert-or-find, pool allocation, entry in
+// the scan's touched list).  Returns the pool index or -1 (error recorded).
+__device__ inline int global_activate(const SubmapDev& m, unsigned long long key) {
+  bool inserted;
+  const int s = hash_activate(m, key, &inserted);
+  if (s < 0) {
+    atomicOr(&m.st->frame_err, kErrCapacity);
+    return -1;
+  }
+  int pool;
+  if (inserted) {
+    pool = atomicAdd(&m.st->n_blocks, 1);
+    if (pool >= m.max_blocks) {
+      atomicOr(&m.st->frame_err, kErrCapacity);
+      atomicExch(m.vals + s, kMapDead);
+      return -1;
+    }
+    m.block_keys[3 * pool] = (int)((key >> 42) & 0x1fffff) - (1 << 20);
+    m.block_keys[3 * pool + 1] = (int)((key >> 21) & 0x1fffff) - (1 << 20);
+    m.block_keys[3 * pool + 2] = (int)(key & 0x1fffff) - (1 << 20);
+    atomicExch(m.vals + s, pool);   // publish
+  } else {
+    pool = *((volatile int32_t*)(m.vals + s));
+    for (long long it = 0; pool == -1 && it < kSpinLimit; ++it) {   // the inserter publishes shortly
+      __nanosleep(64);
+      pool = *((volatile int32_t*)(m.vals + s));
+    }
+    if (pool == -1) {
+      atomicOr(&m.st->frame_err, kErrTimeout);
+      return -1;
+    }
+    if (pool < 0) return -1;
+  }
+  if (*((volatile int32_t*)(m.touch + pool)) == -1 && atomicCAS(m.touch + pool, -1, -2) == -1) {
+    const int j = atomicAdd(&m.st->n_touched, 1);   // j < max_blocks: each block once per scan
+    m.touched[j] = pool;
+    atomicExch(m.touch + pool, j);
+  }
+  return pool;
+}
+
+// Pool index of an already activated block (read-only probe), or -1.
+__device__ __forceinline__ int find_pool(const SubmapDev& m, unsigned long long key) {
+  const int s = hash_find(m, key);
+  if (s < 0) return -1;
+  const int p = __ldg(m.vals + s);
+  return p >= 0 ? p : -1;
+}
+
+// Point index of iteration k of this thread in tile `tile`, or -1.
+__device__ __forceinline__ long long tile_point(const ScanDev& sc, int tile, int k) {
+  const int t = threadIdx.x;
+  if (!sc.organised) {
+    const long long base = (long long)tile * sc.tile_w * sc.tile_h;
+    const long long end = min(base + (long long)sc.tile_w * sc.tile_h, sc.n);
+    const long long i = base + (long long)k * kTileThreads + t;
+    return i < end ? i : -1;
+  }
+  int x, y;
+  if (sc.tile_w == 32) {   // lanes of a warp spread over an 8 x 4 grid of a 32 x 8 chunk
+    const int l = t & 31, w = t >> 5;
+    x = (l & 7) * 4 + (w & 3);
+    y = k * 8 + (l >> 3) * 2 + (w >> 2);
+  } else {
+    const int p = k * kTileThreads + t;
+    x = p % sc.tile_w;
+    y = p / sc.tile_w;
+  }
+  const int gx = (tile % sc.tiles_x) * sc.tile_w + x;
+  const int gy = (tile / sc.tiles_x) * sc.tile_h + y;
+  if (gx >= sc.width || gy >= sc.height || y >= sc.tile_h) return -1;
+  return (long long)gy * sc.width + gx;
+}
+
+__device__ __forceinline__ int tile_iters(const ScanDev& sc) {
+  return (sc.tile_w * sc.tile_h + kTileThreads - 1) / kTileThreads;
+}
+
+// ------------------------------------------------ count + allocate + process
+// One pass per tile.  Each point's band is traversed once; at every block
+// boundary the block key is looked up in a small shared-memory map whose
+// position is the block's slot of per-voxel sums: a new key is claimed with a
+// single CAS, so lookups never wait.  Observations add w*d and w to the slot
+// with shared atomics.  After the pass the tile's distinct blocks (its count
+// phase) are activated once each in the block hash (Sec. III-B "activate":
+// insert-or-find, pool index by atomic bump, entry in the scan's touched list:
+// Sec. III-D allocation phase) and the slots are flushed with vector atomics
+// into the blocks' per-scan accumulators.  A block that finds the map full is
+// activated on the spot and accumulated straight into global memory.
+struct TileSmem {
+  unsigned long long* mkey;   // [lb] block key of each slot, kEmptyKey if free
+  int* pool;                  // [lb]
+  float* swd;                 // [lb * 512]
+  float* sw;                  // [lb * 512]
+  unsigned long long* red;    // [2 * warps]
+};
+
+__host__ __device__ inline size_t tile_smem_bytes(int lb) {
+  return (size_t)lb * 8 + (size_t)lb * 4 + 2 * (kTileThreads / 32) * 8 + 16 + (size_t)lb * kVoxPerBlock * 8;
+}
+
+__device__ inline TileSmem tile_smem(char* base, int lb) {
+  TileSmem t;
+  t.swd = reinterpret_cast<float*>(base);
+  base += (size_t)lb * kVoxPerBlock * 4;
+  t.sw = reinterpret_cast<float*>(base);
+  base += (size_t)lb * kVoxPerBlock * 4;
+  t.mkey = reinterpret_cast<unsigned long long*>(base);
+  base += (size_t)lb * 8;
+  t.red = reinterpret_cast<unsigned long long*>(base);
+  base += 2 * (kTileThreads / 32) * 8;
+  t.pool = reinterpret_cast<int*>(base);
+  return t;
+}
+
+__device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
+  return ((uint32_t)key ^ (uint32_t)(key >> 29)) * 0x9E3779B1u;
+}
+
+// Shared slot of a block in a map of lb (power of two) slots, or -1 if full.
+__device__ __forceinline__ int local_slot(const TileSmem& t, int lb, unsigned long long key) {
+  const uint32_t h = slot_hash(key) >> 16;
+  for (int p = 0; p < lb; ++p) {
+    const int q = (h + p) & (lb - 1);
+    unsigned long long cur = *((volatile unsigned long long*)(t.mkey + q));
+    if (cur == kEmptyKey) {
+      cur = atomicCAS(t.mkey + q, kEmptyKey, key);
+      if (cur == kEmptyKey) return q;
+    }
+    if (cur == key) return q;
+  }
+  return -1;
+}
+
+__device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+  const TileSmem t = tile_smem(smem, lb);
+  const int tid = threadIdx.x;
+  for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
+  {
+    float4* z = reinterpret_cast<float4*>(t.swd);
+    const int n4 = lb * kVoxPerBlock * 2 / 4;
+    for (int q = tid; q < n4; q += kTileThreads) z[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+
+  const float inv_drop = 1.0f / (m.trunc - m.vs);
+  unsigned long long n_obs = 0, n_valid = 0;
+  const int iters = tile_iters(sc);
+  for (int k = 0; k < iters; ++k) {
+    const long long i = tile_point(sc, tile, k);
+    if (i < 0) continue;
+    Ray r;
+    if (!make_ray(sc, i, r)) continue;
+    float A[3], B[3];
+    if (!band(r, m.trunc, m.inv_vs, A, B)) {
+      atomicOr(&m.st->frame_err, kErrKeyRange);
+      continue;
+    }
+    ++n_valid;
+    const float w0 = base_weight(sc, i, r);
+    Dda d;
+    d.init(A, B);
+    int cb0 = 0x7fffffff, cb1 = 0, cb2 = 0;
+    int slot = -1, gpool = -1;
+    for (;;) {
+      const int b0 = d.v[0] >> 3, b1 = d.v[1] >> 3, b2 = d.v[2] >> 3;
+      if (b0 != cb0 || b1 != cb1 || b2 != cb2) {
+        cb0 = b0; cb1 = b1; cb2 = b2;
+        const unsigned long long key = pack_key(b0, b1, b2);
+        slot = local_slot(t, lb, key);
+        gpool = slot < 0 ? global_activate(m, key) : -1;
+      }
+      const float dist = voxel_distance(r, d.v, m.vs, m.trunc);
+      float w = w0;
+      if (sc.dropoff != 0 && dist < -m.vs) {
+        const float f = fmaxf((m.trunc + dist) * inv_drop, 0.0f);
+        w = sc.dropoff == 1 ? w * f : w * f * f;
+      }
+      const int l = local_index(d.v);
+      if (slot >= 0) {
+        atomicAdd(t.swd + slot * kVoxPerBlock + l, w * dist);
+        atomicAdd(t.sw + slot * kVoxPerBlock + l, w);
+      } else if (gpool >= 0) {
+        atomicAdd(m.acc + (size_t)gpool * kVoxPerBlock + l, make_float2(w * dist, w));
+      }
+      ++n_obs;
+      if (d.left == 0) break;
+      d.step();
+    }
+  }
+  __syncthreads();
+  // allocation: each distinct block of the tile is activated once
+  for (int q = tid; q < lb; q += kTileThreads) {
+    const unsigned long long key = t.mkey[q];
+    t.pool[q] = key == kEmptyKey ? -1 : global_activate(m, key);
+  }
+  __syncthreads();
+  // flush the tile's sums into the per-scan accumulators
+  for (int q = 0; q < lb; ++q) {
+    const int pool = t.pool[q];
+    if (pool < 0) continue;
+    float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
+    for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
+      const float w = t.sw[q * kVoxPerBlock + v];
+      if (w != 0.0f) atomicAdd(dst + v, make_float2(t.swd[q * kVoxPerBlock + v], w));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n_obs += __shfl_xor_sync(0xffffffffu, n_obs, o);
+    n_valid += __shfl_xor_sync(0xffffffffu, n_valid, o);
+  }
+  if ((tid & 31) == 0) {
+    t.red[tid >> 5] = n_obs;
+    t.red[kTileThreads / 32 + (tid >> 5)] = n_valid;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long a = 0, c = 0;
+    for (int w = 0; w < kTileThreads / 32; ++w) {
+      a += t.red[w];
+      c += t.red[kTileThreads / 32 + w];
+    }
+    if (a) atomicAdd(&m.st->obs, a);
+    if (c) atomicAdd(&m.st->valid_pts, c);
+  }
+  __syncthreads();   // shared memory is reused by the caller's next tile
+}
+
+// ------------------------------------------------------------- merge
+constexpr int kMergeThreads = 128;   // 4 voxels per thread
+
+template <int kStore>
+struct Vox4;
+
+template <>
+struct Vox4<0> {
+  static __device__ __forceinline__ void load(const SubmapDev& m, size_t e, float D[4], float W[4]) {
+    const float4 d = *reinterpret_cast<const float4*>((const float*)m.D + e);
+    const float4 w = *reinterpret_cast<const float4*>((const float*)m.W + e);
+    D[0] = d.x; D[1] = d.y; D[2] = d.z; D[3] = d.w;
+    W[0] = w.x; W[1] = w.y; W[2] = w.z; W[3] = w.w;
+  }
+  static __device__ __forceinline__ void store(const SubmapDev& m, size_t e, const float D[4], const float W[4]) {
+    *reinterpret_cast<float4*>((float*)m.D + e) = make_float4(D[0], D[1], D[2], D[3]);
+    *reinterpret_cast<float4*>((float*)m.W + e) = make_float4(W[0], W[1], W[2], W[3]);
+  }
+};
+
+template <>
+struct Vox4<1> {   // FP16 storage: D / trunc and W as IEEE half, FP32 arithmetic
+  static __device__ __forceinline__ void load(const SubmapDev& m, size_t e, float D[4], float W[4]) {
+    const uint2 d = *reinterpret_cast<const uint2*>((const __half*)m.D + e);
+    const uint2 w = *reinterpret_cast<const uint2*>((const __half*)m.W + e);
+    const __half2* dh = reinterpret_cast<const __half2*>(&d);
+    const __half2* wh = reinterpret_cast<const __half2*>(&w);
+    const float2 d0 = __half22float2(dh[0]), d1 = __half22float2(dh[1]);
+    const float2 w0 = __half22float2(wh[0]), w1 = __half22float2(wh[1]);
+    D[0] = d0.x * m.trunc; D[1] = d0.y * m.trunc; D[2] = d1.x * m.trunc; D[3] = d1.y * m.trunc;
+    W[0] = w0.x; W[1] = w0.y; W[2] = w1.x; W[3] = w1.y;
+  }
+  static __device__ __forceinline__ void store(const SubmapDev& m, size_t e, const float D[4], const float W[4]) {
+    uint2 d, w;
+    __half2* dh = reinterpret_cast<__half2*>(&d);
+    __half2* wh = reinterpret_cast<__half2*>(&w);
+    dh[0] = __halves2half2(__float2half_rn(D[0] / m.trunc), __float2half_rn(D[1] / m.trunc));
+    dh[1] = __halves2half2(__float2half_rn(D[2] / m.trunc), __float2half_rn(D[3] / m.trunc));
+    wh[0] = __halves2half2(__float2half_rn(W[0]), __float2half_rn(W[1]));
+    wh[1] = __halves2half2(__float2half_rn(W[2]), __float2half_rn(W[3]));
+    *reinterpret_cast<uint2*>((__half*)m.D + e) = d;
+    *reinterpret_cast<uint2*>((__half*)m.W + e) = w;
+  }
+};
+
+// Merge the sums of touched block j (kMergeThreads threads); returns the
+// number of voxels merged by this thread.
+template <int kStore>
+__device__ __forceinline__ int merge_block(const SubmapDev& m, int j, bool skip) {
+  const int tid = threadIdx.x;
+  const int pool = m.touched[j];
+  float4* a = reinterpret_cast<float4*>(m.acc + (size_t)pool * kVoxPerBlock) + 2 * tid;
+  const float4 a0 = a[0], a1 = a[1];
+  const float swd[4] = {a0.x, a0.z, a1.x, a1.z};
+  const float sw[4] = {a0.y, a0.w, a1.y, a1.w};
+  int merged = 0;
+  if ((sw[0] != 0.0f) | (sw[1] != 0.0f) | (sw[2] != 0.0f) | (sw[3] != 0.0f)) {
+    if (!skip) {
+      const size_t e = (size_t)pool * kVoxPerBlock + 4 * tid;
+      float D[4], W[4];
+      Vox4<kStore>::load(m, e, D, W);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (sw[q] != 0.0f) {
+          const float wn = W[q] + sw[q];
+          D[q] = (D[q] * W[q] + swd[q]) / wn;
+          W[q] = fminf(wn, m.max_w);
+          ++merged;
+        }
+      }
+      Vox4<kStore>::store(m, e, D, W);
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    a[0] = z;
+    a[1] = z;
+  }
+  if (tid == 0) m.touch[pool] = -1;
+  return merged;
+}
+
+}  // namespace covox

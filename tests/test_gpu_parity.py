@@ -185,3 +185,11 @@ def test_cudamalloc_path_and_reset():
              for i, x in enumerate(sub.extract()))
     assert sorted(map(tuple, k1)) == sorted(map(tuple, g[0]))
     compare((g[0], g[1], g[2], None, 0), run_oracle(wl)[0], D_TOL_F32)
+
+
+@pytest.mark.parametrize("ppc,lb", [(256, 16), (1024, 2), (2048, 32), (512, 1)])
+def test_organised_tiles_and_local_slot_overflow(ppc, lb):
+    """Organised tiling at several tile heights; few shared-memory block slots
+    force the direct global-accumulation path."""
+    wl = sg.make_c2(n_frames=2, width=320, height=240)
+    compare(run_gpu(wl, pts_per_cta=ppc, local_blocks=lb)[0], run_oracle(wl)[0], D_TOL_F32)
