@@ -215,6 +215,14 @@ __device__ __forceinline__ float voxel_distance(const Ray& r, const int v[3], fl
   return fminf(fmaxf(d, -trunc), trunc);
 }
 
+// Unclamped d of the same definition.
+__device__ __forceinline__ float voxel_distance_raw(const Ray& r, const int v[3], float vs) {
+  const float q0 = fmaf(-((float)v[0] + 0.5f), vs, r.p[0]);
+  const float q1 = fmaf(-((float)v[1] + 0.5f), vs, r.p[1]);
+  const float q2 = fmaf(-((float)v[2] + 0.5f), vs, r.p[2]);
+  return fmaf(q2, r.u[2], fmaf(q1, r.u[1], q0 * r.u[0]));
+}
+
 __device__ __forceinline__ float base_weight(const ScanDev& sc, long long i, const Ray& r) {
   if (sc.weight_mode == 0) return 1.0f;
   if (sc.weight_mode == 2) return __ldg(sc.pw + i);

@@ -79,7 +79,14 @@ __device__ __forceinline__ long long tile_point(const ScanDev& sc, int tile, int
     return i < end ? i : -1;
   }
   int x, y;
-  if (sc.tile_w == 32) {   // lanes of a warp spread over an 8 x 4 grid of a 32 x 8 chunk
+  if (sc.tile_w == 32 && (sc.tile_h & 31) == 0) {
+    // lanes of a warp on an 8 x 4 grid spaced 4 x 8 pixels over a 32 x 32 chunk:
+    // neighbouring lanes rarely share a voxel, so shared atomics rarely collide
+    const int l = t & 31, w = t >> 5;
+    const int c = k & 3;   // 4 iterations of 8 warps fill the 4 x 8 cell
+    x = (l & 7) * 4 + (w & 3);
+    y = (k >> 2) * 32 + (l >> 3) * 8 + (w >> 2) * 4 + c;
+  } else if (sc.tile_w == 32) {   // lanes on an 8 x 4 grid of a 32 x 8 chunk
     const int l = t & 31, w = t >> 5;
     x = (l & 7) * 4 + (w & 3);
     y = k * 8 + (l >> 3) * 2 + (w >> 2);
@@ -141,6 +148,7 @@ __device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
 
 // Shared slot of a block in a map of lb (power of two) slots, or -1 if full.
 __device__ __forceinline__ int local_slot(const TileSmem& t, int lb, unsigned long long key) {
+  if (lb == 0) return -1;
   const uint32_t h = slot_hash(key) >> 16;
   for (int p = 0; p < lb; ++p) {
     const int q = (h + p) & (lb - 1);
@@ -154,6 +162,8 @@ __device__ __forceinline__ int local_slot(const TileSmem& t, int lb, unsigned lo
   return -1;
 }
 
+// lb == 0: no shared slots, every observation is a vector atomic on the
+// block's global per-scan sums (the L2 performs the float additions).
 __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
   const TileSmem t = tile_smem(smem, lb);
   const int tid = threadIdx.x;
@@ -182,32 +192,54 @@ __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int
     const float w0 = base_weight(sc, i, r);
     Dda d;
     d.init(A, B);
-    int cb0 = 0x7fffffff, cb1 = 0, cb2 = 0;
-    int slot = -1, gpool = -1;
+    n_obs += d.left + 1;
+    // incremental state: distance (exact at the first voxel, then one add per
+    // step), local voxel index and packed block key
+    float dist = voxel_distance_raw(r, d.v, m.vs);
+    const float dd0 = -(float)d.s[0] * m.vs * r.u[0];
+    const float dd1 = -(float)d.s[1] * m.vs * r.u[1];
+    const float dd2 = -(float)d.s[2] * m.vs * r.u[2];
+    int l = local_index(d.v);
+    unsigned long long key = pack_key(d.v[0] >> 3, d.v[1] >> 3, d.v[2] >> 3);
+    int slot = local_slot(t, lb, key);
+    int gpool = slot < 0 ? global_activate(m, key) : -1;
     for (;;) {
-      const int b0 = d.v[0] >> 3, b1 = d.v[1] >> 3, b2 = d.v[2] >> 3;
-      if (b0 != cb0 || b1 != cb1 || b2 != cb2) {
-        cb0 = b0; cb1 = b1; cb2 = b2;
-        const unsigned long long key = pack_key(b0, b1, b2);
+      const float dc = fminf(fmaxf(dist, -m.trunc), m.trunc);
+      float w = w0;
+      if (sc.dropoff != 0 && dc < -m.vs) {
+        const float f = fmaxf((m.trunc + dc) * inv_drop, 0.0f);
+        w = sc.dropoff == 1 ? w * f : w * f * f;
+      }
+      if (slot >= 0) {
+        atomicAdd(t.swd + slot * kVoxPerBlock + l, w * dc);
+        atomicAdd(t.sw + slot * kVoxPerBlock + l, w);
+      } else if (gpool >= 0) {
+        atomicAdd(m.acc + (size_t)gpool * kVoxPerBlock + l, make_float2(w * dc, w));
+      }
+      if (d.left == 0) break;
+      // next axis: the traversal rule of Dda::step, as selects
+      const bool a0 = d.v[0] != d.e[0], a1 = d.v[1] != d.e[1], a2 = d.v[2] != d.e[2];
+      int best = a0 ? 0 : (a1 ? 1 : 2);
+      float bt = a0 ? d.tm[0] : (a1 ? d.tm[1] : d.tm[2]);
+      if (a1 && d.tm[1] < bt) { best = 1; bt = d.tm[1]; }
+      if (a2 && d.tm[2] < bt) best = 2;
+      --d.left;
+      int sk, stride, shift;
+      if (best == 0) {
+        sk = d.s[0]; d.v[0] += sk; d.tm[0] = __fadd_rn(d.tm[0], d.td[0]); dist += dd0; stride = 1; shift = 42;
+      } else if (best == 1) {
+        sk = d.s[1]; d.v[1] += sk; d.tm[1] = __fadd_rn(d.tm[1], d.td[1]); dist += dd1; stride = 8; shift = 21;
+      } else {
+        sk = d.s[2]; d.v[2] += sk; d.tm[2] = __fadd_rn(d.tm[2], d.td[2]); dist += dd2; stride = 64; shift = 0;
+      }
+      const int mask = 7 * stride;
+      const int f = ((l & mask) + sk * stride) & mask;
+      l = (l & ~mask) | f;
+      if (f == (sk > 0 ? 0 : mask)) {   // crossed into the neighbouring block
+        key += sk > 0 ? (1ull << shift) : (0ull - (1ull << shift));
         slot = local_slot(t, lb, key);
         gpool = slot < 0 ? global_activate(m, key) : -1;
       }
-      const float dist = voxel_distance(r, d.v, m.vs, m.trunc);
-      float w = w0;
-      if (sc.dropoff != 0 && dist < -m.vs) {
-        const float f = fmaxf((m.trunc + dist) * inv_drop, 0.0f);
-        w = sc.dropoff == 1 ? w * f : w * f * f;
-      }
-      const int l = local_index(d.v);
-      if (slot >= 0) {
-        atomicAdd(t.swd + slot * kVoxPerBlock + l, w * dist);
-        atomicAdd(t.sw + slot * kVoxPerBlock + l, w);
-      } else if (gpool >= 0) {
-        atomicAdd(m.acc + (size_t)gpool * kVoxPerBlock + l, make_float2(w * dist, w));
-      }
-      ++n_obs;
-      if (d.left == 0) break;
-      d.step();
     }
   }
   __syncthreads();

@@ -54,9 +54,9 @@ inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t
   if (ip->sensor != 0 && ip->sensor != 1) return CVX_ERR_INVALID_ARG;
   if (!(ip->min_range >= 0) || !(ip->max_range >= ip->min_range)) return CVX_ERR_INVALID_ARG;
   if (ip->pts_per_cta < 0 || ip->pts_per_cta > (1 << 16)) return CVX_ERR_INVALID_ARG;
-  if (ip->local_blocks < 0 || ip->local_blocks > kMaxLocalBlocks ||
-      (ip->local_blocks & (ip->local_blocks - 1)) != 0)
-    return CVX_ERR_INVALID_ARG;   // a power of two
+  if (ip->local_blocks < -1 || ip->local_blocks > kMaxLocalBlocks ||
+      (ip->local_blocks > 0 && (ip->local_blocks & (ip->local_blocks - 1)) != 0))
+    return CVX_ERR_INVALID_ARG;   // -1, 0 or a power of two
   if (ip->height < 0 || ip->width < 0) return CVX_ERR_INVALID_ARG;
   if (n > (1ll << 31) - 1) return CVX_ERR_INVALID_ARG;
   std::memset(sc, 0, sizeof(*sc));
@@ -88,7 +88,7 @@ inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t
     sc->tiles_x = 1;
     sc->n_tiles = (int)((n + run - 1) / run);
   }
-  *lb = ip->local_blocks > 0 ? ip->local_blocks : kDefaultLocalBlocks;
+  *lb = ip->local_blocks > 0 ? ip->local_blocks : (ip->local_blocks < 0 ? 0 : kDefaultLocalBlocks);
   return CVX_OK;
 }
 

@@ -193,3 +193,9 @@ def test_organised_tiles_and_local_slot_overflow(ppc, lb):
     force the direct global-accumulation path."""
     wl = sg.make_c2(n_frames=2, width=320, height=240)
     compare(run_gpu(wl, pts_per_cta=ppc, local_blocks=lb)[0], run_oracle(wl)[0], D_TOL_F32)
+
+
+def test_global_accumulation_mode_lidar():
+    """local_blocks = -1: every observation goes straight to the global sums."""
+    wl = sg.make_c3(n_scans=4, scans_per_submap=4, n_boxes=300)
+    compare(run_gpu(wl, local_blocks=-1)[0], run_oracle(wl)[0], D_TOL_F32)
