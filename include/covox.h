@@ -152,6 +152,52 @@ void cvx_destroy(cvx_submap* map);
 /* Library version string. */
 const char* cvx_version(void);
 
+/* ---- integration without device allocation ----
+ * No counterpart in the paper: an addition for callers that cannot allocate
+ * device memory -- a real-time loop that must never allocate after start-up,
+ * a host whose memory manager owns all device memory and hands out fixed
+ * buffers, or a plugin that may not touch the process's allocator.
+ *
+ * cvx_integrate_scan_noalloc() integrates one scan, with the same arithmetic
+ * and results as cvx_integrate_scan() on float32 storage, into submap storage
+ * the caller owns and describes with a cvx_submap_view.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its per-scan scratch
+ * (per-voxel sums and touched-block list, about 16.1 MiB) is one fixed array
+ * in device memory that every GPU loading this library holds until the
+ * process exits.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress) and sets a kernel
+ *     attribute; make that first call before any stream capture.
+ *   - All calls on a device share the array.  Each call clears what must
+ *     start at zero, so calls that overlap on the GPU (different streams, or
+ *     different views at the same time) race: serialise them.
+ *   - view->max_blocks above CVX_NOALLOC_MAX_BLOCKS is rejected with
+ *     CVX_ERR_CAPACITY before anything is launched; other invalid arguments
+ *     give CVX_ERR_INVALID_ARG.  Device errors behave as in
+ *     cvx_integrate_scan() and are recorded in the view's state buffer.
+ * Caller initialisation of a view: hash_keys all bits set (0xff bytes),
+ * hash_vals -1 (0xff bytes), dist and weight zero, state zero.  The number of
+ * allocated blocks is the first int32 of the state buffer; blocks are in
+ * allocation order in block_keys / dist / weight. */
+#define CVX_NOALLOC_MAX_BLOCKS 4096
+#define CVX_SUBMAP_STATE_BYTES 128
+
+typedef struct {
+  unsigned long long* hash_keys; /* device [hash_slots] */
+  int32_t* hash_vals;            /* device [hash_slots] */
+  int64_t hash_slots;            /* power of two >= 2 */
+  int32_t* block_keys;           /* device [max_blocks,3] */
+  float* dist;                   /* device [max_blocks,512], D in metres */
+  float* weight;                 /* device [max_blocks,512], W */
+  void* state;                   /* device, CVX_SUBMAP_STATE_BYTES bytes */
+  int64_t max_blocks;            /* <= CVX_NOALLOC_MAX_BLOCKS */
+  float voxel_size, trunc, max_weight;
+} cvx_submap_view;
+
+cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, const float* points_xyz, int64_t n,
+                                      const float T_sub_sensor[12], const float* point_weights,
+                                      const cvx_integrate_params* params, void* stream);
+
 /* ---- tracing: launch accounting and per-kernel timing ----
  * Every kernel launch of the library is counted.  While profiling is on, an
  * event pair is recorded on the launching stream around each launch (up to

@@ -60,6 +60,17 @@ class cvx_counters(ctypes.Structure):
                 ("voxels_merged", ctypes.c_int64), ("blocks_touched", ctypes.c_int64)]
 
 
+class cvx_submap_view(ctypes.Structure):
+    _fields_ = [("hash_keys", ctypes.c_void_p), ("hash_vals", ctypes.c_void_p),
+                ("hash_slots", ctypes.c_int64), ("block_keys", ctypes.c_void_p),
+                ("dist", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("state", ctypes.c_void_p),
+                ("max_blocks", ctypes.c_int64), ("voxel_size", ctypes.c_float),
+                ("trunc", ctypes.c_float), ("max_weight", ctypes.c_float)]
+
+
+CVX_NOALLOC_MAX_BLOCKS = 4096
+CVX_SUBMAP_STATE_BYTES = 128
+
 _lock = threading.Lock()
 _lib = None
 
@@ -74,6 +85,8 @@ SIGNATURES = {
     "cvx_submap_status": (_i32, [_vp]),
     "cvx_submap_counters": (_i32, [_vp, ctypes.POINTER(cvx_counters)]),
     "cvx_destroy": (None, [_vp]),
+    "cvx_integrate_scan_noalloc": (_i32, [ctypes.POINTER(cvx_submap_view), _vp, _i64, _vp, _vp,
+                                          ctypes.POINTER(cvx_integrate_params), _vp]),
     "cvx_profile_start": (_i32, [_i64]),
     "cvx_profile_stop": (_i32, []),
     "cvx_profile_read": (_i32, [_i32, _vp, _vp, _vp]),
@@ -138,6 +151,17 @@ def cvx_integrate_scan(handle: int, points, T_sub_sensor, point_weights, params:
     T = np.ascontiguousarray(T_sub_sensor, dtype=np.float32).reshape(12)
     check(lib().cvx_integrate_scan(handle, pp, n, T.ctypes.data_as(ctypes.c_void_p), pw,
                                    ctypes.byref(params), _stream_handle(stream)), "cvx_integrate_scan")
+
+
+def cvx_integrate_scan_noalloc(view: cvx_submap_view, points, T_sub_sensor, point_weights,
+                               params: cvx_integrate_params, stream=None) -> int:
+    """Returns the status (no exception) so callers can see CVX_ERR_CAPACITY."""
+    n = int(points.shape[0])
+    pp = _dev_ptr(points, "torch.float32", "points") if n else None
+    pw = None if point_weights is None else _dev_ptr(point_weights, "torch.float32", "point_weights")
+    T = np.ascontiguousarray(T_sub_sensor, dtype=np.float32).reshape(12)
+    return int(lib().cvx_integrate_scan_noalloc(ctypes.byref(view), pp, n, T.ctypes.data_as(ctypes.c_void_p),
+                                                pw, ctypes.byref(params), _stream_handle(stream)))
 
 
 def cvx_extract_blocks(handle: int, capacity: int, keys, dist, weight, stream=None) -> int:
