@@ -152,6 +152,48 @@ void cvx_destroy(cvx_submap* map);
 /* Library version string. */
 const char* cvx_version(void);
 
+/* ---- batched integration: many submaps, uneven scans, one persistent launch ----
+ * A scan of a batch: which submap it goes to (index into the maps array of
+ * cvx_integrate_batch), its points (device float32 [n,3], sensor frame), pose
+ * (host float32 3x4 submap <- sensor), optional per-point weights (device
+ * [n]) and integration parameters, all as for cvx_integrate_scan. */
+typedef struct {
+  int32_t submap;
+  int32_t pad;
+  const float* points_xyz;
+  int64_t n;
+  float T_sub_sensor[12];
+  const float* point_weights;
+  cvx_integrate_params params;
+} cvx_scan_desc;
+
+typedef struct cvx_batch cvx_batch;
+
+/* Descriptor buffers for batches of up to max_submaps submaps (<= 1024) and
+ * max_scans scans (device memory and pinned host staging).  Synchronous. */
+cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** out);
+
+/* Integrate a batch of scans into distinct submaps with one cooperative
+ * persistent kernel (Sec. III-D workload equalisation across scans).  Scans
+ * of one submap are integrated as successive frames in array order (exactly
+ * as successive cvx_integrate_scan calls); scans of different submaps are
+ * independent; empty scans are skipped.  The scans' tiles of each wave (the
+ * k-th scan of every submap) are spread over all SMs, then all touched blocks
+ * are merged.  Asynchronous on `stream`; the descriptor upload reads the
+ * batch object's pinned staging buffer when the stream executes it, so a CUDA
+ * graph that captured this call replays the staging buffer's contents at
+ * replay time: do not issue another call on the same batch object between
+ * replays.  Grid barriers inside the kernel are bounded; a barrier that gives
+ * up is reported by cvx_batch_error() as CVX_ERR_TIMEOUT, after which the
+ * batch's submaps must be reset. */
+cvx_status cvx_integrate_batch(cvx_batch* batch, cvx_submap* const* maps, int32_t n_maps,
+                               const cvx_scan_desc* scans, int32_t n_scans, void* stream);
+
+/* CVX_ERR_TIMEOUT if a barrier of the last batch gave up (synchronous). */
+int32_t cvx_batch_error(cvx_batch* batch);
+
+void cvx_batch_destroy(cvx_batch* batch);
+
 /* ---- integration without device allocation ----
  * No counterpart in the paper: an addition for callers that cannot allocate
  * device memory -- a real-time loop that must never allocate after start-up,

@@ -60,6 +60,12 @@ class cvx_counters(ctypes.Structure):
                 ("voxels_merged", ctypes.c_int64), ("blocks_touched", ctypes.c_int64)]
 
 
+class cvx_scan_desc(ctypes.Structure):
+    _fields_ = [("submap", ctypes.c_int32), ("pad", ctypes.c_int32), ("points_xyz", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("T_sub_sensor", ctypes.c_float * 12),
+                ("point_weights", ctypes.c_void_p), ("params", cvx_integrate_params)]
+
+
 class cvx_submap_view(ctypes.Structure):
     _fields_ = [("hash_keys", ctypes.c_void_p), ("hash_vals", ctypes.c_void_p),
                 ("hash_slots", ctypes.c_int64), ("block_keys", ctypes.c_void_p),
@@ -87,6 +93,10 @@ SIGNATURES = {
     "cvx_destroy": (None, [_vp]),
     "cvx_integrate_scan_noalloc": (_i32, [ctypes.POINTER(cvx_submap_view), _vp, _i64, _vp, _vp,
                                           ctypes.POINTER(cvx_integrate_params), _vp]),
+    "cvx_batch_create": (_i32, [_i32, _i32, ctypes.POINTER(_vp)]),
+    "cvx_integrate_batch": (_i32, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(cvx_scan_desc), _i32, _vp]),
+    "cvx_batch_error": (_i32, [_vp]),
+    "cvx_batch_destroy": (None, [_vp]),
     "cvx_profile_start": (_i32, [_i64]),
     "cvx_profile_stop": (_i32, []),
     "cvx_profile_read": (_i32, [_i32, _vp, _vp, _vp]),
@@ -151,6 +161,38 @@ def cvx_integrate_scan(handle: int, points, T_sub_sensor, point_weights, params:
     T = np.ascontiguousarray(T_sub_sensor, dtype=np.float32).reshape(12)
     check(lib().cvx_integrate_scan(handle, pp, n, T.ctypes.data_as(ctypes.c_void_p), pw,
                                    ctypes.byref(params), _stream_handle(stream)), "cvx_integrate_scan")
+
+
+def cvx_batch_create(max_submaps: int, max_scans: int) -> int:
+    h = ctypes.c_void_p()
+    check(lib().cvx_batch_create(max_submaps, max_scans, ctypes.byref(h)), "cvx_batch_create")
+    return h.value
+
+
+def cvx_integrate_batch(batch: int, maps, scans, stream=None) -> None:
+    """maps: submap handles; scans: list of (submap index, points tensor,
+    T (12 floats), point_weights tensor or None, cvx_integrate_params)."""
+    arr_maps = (ctypes.c_void_p * len(maps))(*maps)
+    descs = (cvx_scan_desc * max(len(scans), 1))()
+    for k, (mi, pts, T, pw, prm) in enumerate(scans):
+        n = int(pts.shape[0])
+        descs[k].submap = int(mi)
+        descs[k].points_xyz = _dev_ptr(pts, "torch.float32", "points") if n else None
+        descs[k].n = n
+        descs[k].T_sub_sensor[:] = [float(x) for x in np.asarray(T, dtype=np.float32).reshape(12)]
+        descs[k].point_weights = None if pw is None else _dev_ptr(pw, "torch.float32", "point_weights")
+        descs[k].params = prm
+    check(lib().cvx_integrate_batch(batch, arr_maps, len(maps), descs, len(scans), _stream_handle(stream)),
+          "cvx_integrate_batch")
+
+
+def cvx_batch_error(batch: int) -> int:
+    return int(lib().cvx_batch_error(batch))
+
+
+def cvx_batch_destroy(batch: int) -> None:
+    if batch:
+        lib().cvx_batch_destroy(batch)
 
 
 def cvx_integrate_scan_noalloc(view: cvx_submap_view, points, T_sub_sensor, point_weights,

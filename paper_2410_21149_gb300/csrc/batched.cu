@@ -1,0 +1,350 @@
+// batched.cu -- many submaps and scans of uneven size in one persistent launch.
+//
+// Scans of one submap are frames in the order given; scans of different
+// submaps are independent (submaps are separate maps, coVoxSLAM Sec. III-C).
+// The host groups the scans into waves (wave k = the k-th scan of every
+// submap that has one) and one cooperative kernel walks the waves:
+//   phase 1  every tile of every scan of the wave: integrate_tile (count,
+//            allocate, per-voxel sums; Sec. III-D), tiles spread over all
+//            CTAs so uneven scans share the GPU (workload equalisation);
+//   phase 2  every touched block of every submap of the wave: merge_block;
+//   phase 3  per-submap bookkeeping of the frame (counters, error words).
+// Phases are separated by grid barriers whose spins are bounded: a barrier
+// that gives up records CVX_ERR_TIMEOUT and every CTA leaves the kernel.
+// The arithmetic is the per-scan path's device code, unchanged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/covox.h"
+#include "covox_dev.cuh"
+#include "integrate_dev.cuh"
+#include "prof.h"
+#include "submap.h"
+
+using namespace covox;
+
+namespace {
+
+struct BatchDev {
+  const SubmapDev* maps;   // [n_maps]
+  const ScanDev* scans;    // [n_scans] in wave order
+  const int* scan_map;     // [n_scans] submap of each scan
+  const int* scan_lb;      // [n_scans] shared block slots
+  const int* tile_prefix;  // [n_scans + 1] tiles before each scan (wave order)
+  const int* wave_begin;   // [n_waves + 1] first scan of each wave
+  int n_waves;
+  unsigned* bar_count;
+  unsigned* bar_gen;
+  int* err;
+};
+
+constexpr long long kBarrierSpin = 1ll << 24;   // ~1 s at the sleep below
+constexpr int kMaxWaveScans = 1024;
+
+__device__ bool grid_barrier(const BatchDev& b) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g = *((volatile unsigned*)b.bar_gen);
+    __threadfence();
+    if (atomicAdd(b.bar_count, 1u) == gridDim.x - 1) {
+      *((volatile unsigned*)b.bar_count) = 0;
+      __threadfence();
+      atomicAdd(b.bar_gen, 1u);
+    } else {
+      long long it = 0;
+      while (*((volatile unsigned*)b.bar_gen) == g) {
+        if (++it > kBarrierSpin || *((volatile int*)b.err) != 0) {
+          atomicOr(b.err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ int find_scan(const int* prefix, int lo, int hi, int g) {
+  // largest s in [lo, hi) with prefix[s] <= g
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (prefix[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kTileThreads) batched_kernel(BatchDev b) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int nt_prefix[kMaxWaveScans + 1];
+  const int tid = threadIdx.x;
+  for (int w = 0; w < b.n_waves; ++w) {
+    const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
+    // phase 1: tiles of all scans of the wave
+    const int t0 = b.tile_prefix[s0], total = b.tile_prefix[s1] - t0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      const int s = find_scan(b.tile_prefix, s0, s1, t0 + t);
+      integrate_tile(b.maps[b.scan_map[s]], b.scans[s], t0 + t - b.tile_prefix[s], smem, b.scan_lb[s]);
+    }
+    if (!grid_barrier(b)) return;
+    // phase 2: merge every touched block of every submap of the wave
+    if (tid == 0) {
+      int acc = 0;
+      for (int s = s0; s < s1; ++s) {
+        nt_prefix[s - s0] = acc;
+        const SubmapDev& m = b.maps[b.scan_map[s]];
+        acc += min(*((volatile int32_t*)&m.st->n_touched), m.max_blocks);
+      }
+      nt_prefix[s1 - s0] = acc;
+    }
+    __syncthreads();
+    const int nt_total = nt_prefix[s1 - s0];
+    const int half = tid >> 7, sub = tid & (kMergeThreads - 1);
+    for (int j = 2 * blockIdx.x + half; j < nt_total; j += 2 * gridDim.x) {
+      const int q = find_scan(nt_prefix, 0, s1 - s0, j);
+      const SubmapDev& m = b.maps[b.scan_map[s0 + q]];
+      const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
+      const int merged = m.storage == 0 ? merge_block<0>(m, j - nt_prefix[q], skip, sub)
+                                        : merge_block<1>(m, j - nt_prefix[q], skip, sub);
+      unsigned long long c = merged;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
+    }
+    if (!grid_barrier(b)) return;
+    // phase 3: per-submap bookkeeping of this frame
+    if (blockIdx.x == 0) {
+      for (int s = s0 + tid; s < s1; s += blockDim.x) {
+        State* st = b.maps[b.scan_map[s]].st;
+        st->blocks_touched += (unsigned long long)(nt_prefix[s - s0 + 1] - nt_prefix[s - s0]);
+        st->frames += 1;
+        st->sticky_err |= st->frame_err;
+        st->frame_err = 0;
+        st->n_touched = 0;
+      }
+    }
+    if (!grid_barrier(b)) return;
+  }
+}
+
+}  // namespace
+
+struct cvx_batch {
+  int max_maps, max_scans;
+  void* dev;          // descriptor block on the device
+  void* host;         // pinned staging of the same layout
+  size_t bytes;
+  unsigned* bar;      // count, gen, err (device)
+  cudaEvent_t copied; // host staging reusable once the previous upload ran
+  bool pending;
+  int grid;           // persistent grid size (CTAs)
+  int lb_max;
+};
+
+namespace {
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct Layout {
+  size_t maps, scans, scan_map, scan_lb, tile_prefix, wave_begin, total;
+};
+
+Layout layout(int max_maps, int max_scans) {
+  Layout L;
+  size_t o = 0;
+  L.maps = o;
+  o = align16(o + sizeof(SubmapDev) * max_maps);
+  L.scans = o;
+  o = align16(o + sizeof(ScanDev) * max_scans);
+  L.scan_map = o;
+  o = align16(o + sizeof(int) * max_scans);
+  L.scan_lb = o;
+  o = align16(o + sizeof(int) * max_scans);
+  L.tile_prefix = o;
+  o = align16(o + sizeof(int) * (max_scans + 1));
+  L.wave_begin = o;
+  o = align16(o + sizeof(int) * (max_scans + 1));
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** out) {
+  if (!out || max_submaps <= 0 || max_scans <= 0 || max_submaps > kMaxWaveScans || max_scans > (1 << 20))
+    return CVX_ERR_INVALID_ARG;
+  *out = nullptr;
+  cvx_batch* b = new (std::nothrow) cvx_batch();
+  if (!b) return CVX_ERR_OOM;
+  b->max_maps = max_submaps;
+  b->max_scans = max_scans;
+  const Layout L = layout(max_submaps, max_scans);
+  b->bytes = L.total;
+  if (cudaMalloc(&b->dev, L.total) != cudaSuccess || cudaMallocHost(&b->host, L.total) != cudaSuccess ||
+      cudaMalloc((void**)&b->bar, 16) != cudaSuccess || cudaMemset(b->bar, 0, 16) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (b->dev) cudaFree(b->dev);
+    if (b->host) cudaFreeHost(b->host);
+    if (b->bar) cudaFree(b->bar);
+    delete b;
+    return CVX_ERR_OOM;
+  }
+  b->lb_max = kMaxLocalBlocks;
+  cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)tile_smem_bytes(kMaxLocalBlocks));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kTileThreads,
+                                                    tile_smem_bytes(kDefaultLocalBlocks)) != cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  b->grid = per_sm * num_sms();
+  *out = b;
+  return CVX_OK;
+}
+
+void cvx_batch_destroy(cvx_batch* b) {
+  if (!b) return;
+  cudaEventSynchronize(b->copied);
+  cudaFree(b->dev);
+  cudaFreeHost(b->host);
+  cudaFree(b->bar);
+  cudaEventDestroy(b->copied);
+  delete b;
+}
+
+cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_maps,
+                               const cvx_scan_desc* scans, int32_t n_scans, void* stream) {
+  if (!b || !maps || n_maps <= 0 || n_maps > b->max_maps || n_scans < 0 || n_scans > b->max_scans ||
+      (n_scans > 0 && !scans))
+    return CVX_ERR_INVALID_ARG;
+  for (int q = 0; q < n_maps; ++q)
+    for (int r = 0; r < q; ++r)
+      if (!maps[q] || maps[q] == maps[r]) return CVX_ERR_INVALID_ARG;   // distinct submaps
+  // validate and describe every scan; empty scans are no frames; group the
+  // rest into waves (wave k = k-th non-empty scan of each submap)
+  std::vector<ScanDev> sd(n_scans);
+  std::vector<int> lbs(n_scans), rank(n_scans), per_map(n_maps, 0), order;
+  int n_waves = 0, lb_max = 0;
+  for (int s = 0; s < n_scans; ++s) {
+    const cvx_scan_desc& d = scans[s];
+    if (d.submap < 0 || d.submap >= n_maps) return CVX_ERR_INVALID_ARG;
+    const cvx_status v =
+        make_scan_dev(maps[d.submap], d.points_xyz, d.n, d.T_sub_sensor, d.point_weights, &d.params, &sd[s], &lbs[s]);
+    if (v != CVX_OK) return v;
+    if (d.n == 0) continue;
+    rank[s] = per_map[d.submap]++;
+    n_waves = std::max(n_waves, rank[s] + 1);
+    lb_max = std::max(lb_max, lbs[s]);
+    order.push_back(s);
+  }
+  if (order.empty()) return CVX_OK;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return rank[a] < rank[c]; });
+  const int n_run = (int)order.size();
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  // the staging buffer may still feed the previous upload
+  if (b->pending && !capturing) {
+    if (cudaEventSynchronize(b->copied) != cudaSuccess) {
+      cudaGetLastError();
+      return CVX_ERR_CUDA;
+    }
+    b->pending = false;
+  }
+  const Layout L = layout(b->max_maps, b->max_scans);
+  char* h = (char*)b->host;
+  SubmapDev* hm = (SubmapDev*)(h + L.maps);
+  ScanDev* hs = (ScanDev*)(h + L.scans);
+  int* hmap = (int*)(h + L.scan_map);
+  int* hlb = (int*)(h + L.scan_lb);
+  int* htp = (int*)(h + L.tile_prefix);
+  int* hwb = (int*)(h + L.wave_begin);
+  for (int q = 0; q < n_maps; ++q) hm[q] = maps[q]->dev;
+  int tiles = 0, wave = -1;
+  for (int k = 0; k < n_run; ++k) {
+    const int s = order[k];
+    while (wave < rank[s]) hwb[++wave] = k;
+    hs[k] = sd[s];
+    hmap[k] = scans[s].submap;
+    hlb[k] = lbs[s];
+    htp[k] = tiles;
+    tiles += sd[s].n_tiles;
+  }
+  htp[n_run] = tiles;
+  hwb[n_waves] = n_run;
+  if (cudaMemcpyAsync(b->dev, b->host, L.total, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  if (!capturing) {
+    if (cudaEventRecord(b->copied, st) != cudaSuccess) {
+      cudaGetLastError();
+      return CVX_ERR_CUDA;
+    }
+    b->pending = true;
+  }
+  for (int q = 0; q < n_maps; ++q) maps[q]->last_stream = st;
+  char* d = (char*)b->dev;
+  BatchDev bd;
+  bd.maps = (const SubmapDev*)(d + L.maps);
+  bd.scans = (const ScanDev*)(d + L.scans);
+  bd.scan_map = (const int*)(d + L.scan_map);
+  bd.scan_lb = (const int*)(d + L.scan_lb);
+  bd.tile_prefix = (const int*)(d + L.tile_prefix);
+  bd.wave_begin = (const int*)(d + L.wave_begin);
+  bd.n_waves = n_waves;
+  bd.bar_count = b->bar;
+  bd.bar_gen = b->bar + 1;
+  bd.err = (int*)(b->bar + 2);
+  if (cudaMemsetAsync(b->bar, 0, 16, st) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kTileThreads,
+                                                    tile_smem_bytes(lb_max)) != cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  const int grid = per_sm * num_sms();
+  void* args[] = {&bd};
+  cudaError_t e;
+  COVOX_LAUNCH(kKBatched, st,
+               e = cudaLaunchCooperativeKernel((void*)batched_kernel, dim3(grid), dim3(kTileThreads), args,
+                                               tile_smem_bytes(lb_max), st));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  return CVX_OK;
+}
+
+int32_t cvx_batch_error(cvx_batch* b) {
+  if (!b) return CVX_ERR_INVALID_ARG;
+  unsigned v[3] = {0, 0, 0};
+  if (cudaMemcpy(v, b->bar, 12, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  return (v[2] & kErrTimeout) ? CVX_ERR_TIMEOUT : CVX_OK;
+}
+
+}  // extern "C"

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
   const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
   const int tid = threadIdx.x;
   unsigned long long merged = 0;
-  for (int j = blockIdx.x; j < nt; j += gridDim.x) merged += merge_block<kStore>(m, j, skip);
+  for (int j = blockIdx.x; j < nt; j += gridDim.x) merged += merge_block<kStore>(m, j, skip, tid);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) merged += __shfl_xor_sync(0xffffffffu, merged, o);
   if ((tid & 31) == 0) red[tid >> 5] = merged;

@@ -326,11 +326,10 @@ struct Vox4<1> {   // FP16 storage: D / trunc and W as IEEE half, FP32 arithmeti
   }
 };
 
-// Merge the sums of touched block j (kMergeThreads threads); returns the
-// number of voxels merged by this thread.
+// Merge the sums of touched block j (kMergeThreads threads, this one is
+// `tid`); returns the number of voxels merged by this thread.
 template <int kStore>
-__device__ __forceinline__ int merge_block(const SubmapDev& m, int j, bool skip) {
-  const int tid = threadIdx.x;
+__device__ __forceinline__ int merge_block(const SubmapDev& m, int j, bool skip, int tid) {
   const int pool = m.touched[j];
   float4* a = reinterpret_cast<float4*>(m.acc + (size_t)pool * kVoxPerBlock) + 2 * tid;
   const float4 a0 = a[0], a1 = a[1];

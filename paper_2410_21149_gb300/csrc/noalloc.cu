@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_static_kernel(SubmapDev m
   const int nt = min(*((volatile int32_t*)&m.st->n_touched), m.max_blocks);
   const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
   unsigned long long merged = 0;
-  for (int j = blockIdx.x; j < nt; j += gridDim.x) merged += merge_block<0>(m, j, skip);
+  for (int j = blockIdx.x; j < nt; j += gridDim.x) merged += merge_block<0>(m, j, skip, threadIdx.x);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) merged += __shfl_xor_sync(0xffffffffu, merged, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = merged;

@@ -89,3 +89,55 @@ def compare(gpu, orc, d_tol, w_rel=1e-4, w_floor=1e-6, fp16_trunc=None):
     assert derr.size == 0 or derr.max() <= d_tol, f"D error {derr.max()}"
     return {"d_max": float(derr.max()) if derr.size else 0.0, "w_max": float(werr.max()),
             "voxels": int(both.sum()), "blocks": int(len(ko))}
+
+
+def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=False, **over):
+    """Integrate all submaps of the workload with one cvx_integrate_batch call
+    (scans of a submap are frames in order).  Returns the run_gpu tuple list."""
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import _capi
+    storages = storages or [wl.storage] * len(wl.submaps)
+    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, st, max_blocks=max_blocks)
+            for sm, st in zip(wl.submaps, storages)]
+    keep = []
+    scans = []
+    # interleave submaps' scans (any order works; frames keep per-submap order)
+    k = 0
+    while any(k < len(sm.scans) for sm in wl.submaps):
+        for m, sm in enumerate(wl.submaps):
+            if k < len(sm.scans):
+                sc = sm.scans[k]
+                pts = torch.from_numpy(np.ascontiguousarray(sc.points)).cuda()
+                keep.append(pts)
+                scans.append((m, pts, sc.T_sub_sensor, None, int_params(wl, sc, **over)))
+        k += 1
+    batch = _capi.cvx_batch_create(len(subs), len(scans))
+    handles = [s.handle for s in subs]
+    if graph:
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            _capi.cvx_integrate_batch(batch, handles, scans, s)
+        for sub in subs:
+            sub.reset()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            g.replay()
+        s.synchronize()
+    else:
+        _capi.cvx_integrate_batch(batch, handles, scans)
+    torch.cuda.synchronize()
+    err = _capi.cvx_batch_error(batch)
+    out = []
+    for sm, sub, st in zip(wl.submaps, subs, storages):
+        keys, D, W = sub.extract()
+        keys = keys.cpu().numpy()
+        D = D.cpu().numpy().astype(np.float64)
+        W = W.cpu().numpy().astype(np.float64)
+        if st == 1:
+            D = D * np.float64(np.float32(sm.trunc))
+        out.append((keys, D, W, sub.counters(), sub.status() or err))
+        sub.close()
+    _capi.cvx_batch_destroy(batch)
+    return out

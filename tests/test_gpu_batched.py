@@ -1,0 +1,76 @@
+"""Batched persistent integration (many submaps, uneven mixed scans, one
+cooperative launch) against the CPU oracle and the per-scan path."""
+import numpy as np
+import pytest
+
+import scenegen as sg
+from _harness import compare, run_gpu, run_gpu_batched, run_oracle, sort_blocks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    return sg.make_c4(n_submaps=6, max_scans=4, depth_wh=(160, 120), lidar_rc=(16, 256))
+
+
+def test_batched_mixed_fp32_fp16_vs_oracle(mixed):
+    storages = [m % 2 for m in range(len(mixed.submaps))]
+    g = run_gpu_batched(mixed, storages)
+    for m, (a, st) in enumerate(zip(g, storages)):
+        sm = mixed.submaps[m]
+        sub = sg.Workload(mixed.name, [sm], mixed.max_weight, mixed.weight_mode, mixed.dropoff,
+                          mixed.min_range, mixed.max_range, mixed.scene, st)
+        o = run_oracle(sub, fp16=bool(st))[0]
+        if st:
+            compare(a, o, 1e-3 * sm.trunc, fp16_trunc=sm.trunc)
+        else:
+            compare(a, o, 1e-5)
+        assert a[3]["frames"] == len(sm.scans)
+        assert a[3]["observations"] == o[3]["obs"]
+
+
+def test_batched_equals_per_scan_path():
+    wl = sg.make_c1(n_frames=4)
+    wl2 = sg.make_c3(n_scans=4, scans_per_submap=2, rows=16, cols=256, n_boxes=300)
+    wl.submaps = wl.submaps + wl2.submaps     # room + two LiDAR submaps, voxel sizes differ
+    gb = run_gpu_batched(wl)
+    for m, sm in enumerate(wl.submaps):
+        sub = sg.Workload(wl.name, [sm], wl.max_weight, wl.weight_mode, wl.dropoff, wl.min_range,
+                          wl.max_range, wl.scene, 0)
+        gs = run_gpu(sub)[0]
+        compare(gb[m], (*sort_blocks(gs[0], gs[1], gs[2]), {}), 1e-5)
+
+
+def test_batched_graph_capture_replay(mixed):
+    g = run_gpu_batched(mixed, graph=True)
+    e = run_gpu_batched(mixed)
+    for a, b in zip(g, e):
+        compare(a, (*sort_blocks(b[0], b[1], b[2]), {}), 1e-3 * 0.6, fp16_trunc=0.6)
+
+
+def test_batched_rejects_bad_arguments():
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import _capi
+    sub = cvx.Submap(0.1, 0.3)
+    b = _capi.cvx_batch_create(2, 4)
+    pts = torch.zeros((8, 3), device="cuda")
+    T = np.eye(3, 4, dtype=np.float32)
+    with pytest.raises(cvx.CovoxError):
+        _capi.cvx_integrate_batch(b, [sub.handle, sub.handle], [(0, pts, T, None, cvx.integrate_params())])
+    with pytest.raises(cvx.CovoxError):
+        _capi.cvx_integrate_batch(b, [sub.handle], [(1, pts, T, None, cvx.integrate_params())])
+    # empty scans are not frames
+    _capi.cvx_integrate_batch(b, [sub.handle], [(0, torch.zeros((0, 3), device="cuda"), T, None,
+                                                  cvx.integrate_params())])
+    torch.cuda.synchronize()
+    assert sub.counters()["frames"] == 0 and _capi.cvx_batch_error(b) == 0
+    _capi.cvx_batch_destroy(b)
