@@ -390,6 +390,7 @@ class SubmapWork:
     T_world_sub: np.ndarray   # float64 [3, 4]
     voxel_size: float
     trunc: float
+    scene: Optional["Scene"] = None   # scene the submap's scans see (None: the workload's)
 
 
 @dataclasses.dataclass
@@ -511,7 +512,8 @@ def make_c4(seed: int = 4, n_submaps: int = 32, max_scans: int = 16, depth_wh=(6
                 else:
                     scans.append(Scan(cam.render(indoor, traj_in[k], seed, 300000 + m * 64 + j),
                                       _to_sub(traj_in[k], anchor), 0, H, W))
-        submaps.append(SubmapWork(scans, pose_from(np.eye(3), anchor), vs, tr))
+        submaps.append(SubmapWork(scans, pose_from(np.eye(3), anchor), vs, tr,
+                                  outdoor if outdoor_map else indoor))
     wl = Workload(f"batched-{n_submaps}maps", submaps, 1e4, 0, 0, 0.1, 50.0, indoor, storage=1)
     wl.scenes = {"indoor": indoor, "outdoor": outdoor}
     return wl
