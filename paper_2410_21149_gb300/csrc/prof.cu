@@ -9,7 +9,7 @@
 
 namespace {
 
-const char* kNames[covox::kNumKinds] = {"alloc_kernel",    "accum_kernel",  "merge_kernel",
+const char* kNames[covox::kNumKinds] = {"alloc_kernel",    "integrate_kernel", "merge_kernel",
                                         "zero_pool_kernel", "batched_kernel", "features_kernel",
                                         "mlp_fwd_kernel",  "mlp_bwd_kernel", "adam_kernel",
                                         "targets_kernel"};
