@@ -194,6 +194,49 @@ int32_t cvx_batch_error(cvx_batch* batch);
 
 void cvx_batch_destroy(cvx_batch* batch);
 
+/* ---- learned per-point weight (Sec. III-C weighting paragraph) ----
+ * Features of an organised scan, one row of three per point (device float32
+ * [height*width, 3]): f1 = |P| / max_range; f2 = theta / (pi/2) with theta the
+ * angle between the ray and the surface normal from the cross product of the
+ * horizontal and vertical neighbour differences (0 when a neighbour is
+ * missing); f3 = ln(var + 1e-8) / 10 with var the population variance of the
+ * depths (z for a pinhole, range for a spherical sensor) of the valid points
+ * of the 5x5 window (0 if fewer than 3).  Invalid points get zeros. */
+cvx_status cvx_point_features(const float* points_xyz, int32_t height, int32_t width, int32_t sensor,
+                              float max_range, float* features, void* stream);
+
+/* Weight network w = softplus(W3 . h2 + b3), h2 = relu(W2 h1 + b2),
+ * h1 = relu(W1 f + b1), 3-32-32-1, GEMM operands rounded to BF16 with FP32
+ * accumulation on the tensor cores.  Parameters: float32[CVX_MLP_PARAMS] in
+ * the order W1 [32,3] row-major, b1 [32], W2 [32,32], b2 [32], W3 [32], b3. */
+#define CVX_MLP_PARAMS 1217
+typedef struct cvx_weight_model cvx_weight_model;
+
+/* Device copy of init_params (host or device pointer) plus Adam state. */
+cvx_status cvx_weight_model_create(const float* init_params, cvx_weight_model** out);
+/* Set (set != NULL) and/or read back (get != NULL, synchronous) the parameters. */
+cvx_status cvx_weight_model_params(cvx_weight_model* model, const float* set, float* get, void* stream);
+/* weights[i] = network(features[i]) for n points (device arrays). */
+cvx_status cvx_weight_model_infer(cvx_weight_model* model, const float* features, int64_t n,
+                                  float* weights, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr; lr = 0 only
+ * computes the gradient) on the mean over points with mask != 0 of
+ * w e2 - ln w (Gaussian negative log likelihood of precision w).  The
+ * per-CTA gradient partials are summed in a fixed order: deterministic. */
+cvx_status cvx_weight_model_train_step(cvx_weight_model* model, const float* features, const float* e2,
+                                       const float* mask, int64_t n, float lr, void* stream);
+/* The last step's mean gradient [CVX_MLP_PARAMS] and loss (synchronous). */
+cvx_status cvx_weight_model_last(cvx_weight_model* model, float* grad, float* loss, void* stream);
+void cvx_weight_model_destroy(cvx_weight_model* model);
+
+/* Training targets of a noisy scan against a noise-free float32 submap:
+ * e2[i] = mean over the point's band voxels with clean W > 0 of
+ * (d - D_clean)^2 (d as in cvx_integrate_scan), mask[i] = 1 if there was at
+ * least one such voxel, else e2 = mask = 0.  Device arrays of n floats. */
+cvx_status cvx_training_targets(cvx_submap* clean, const float* points_xyz, int64_t n,
+                                const float T_sub_sensor[12], const cvx_integrate_params* params,
+                                float* e2, float* mask, void* stream);
+
 /* ---- integration without device allocation ----
  * No counterpart in the paper: an addition for callers that cannot allocate
  * device memory -- a real-time loop that must never allocate after start-up,

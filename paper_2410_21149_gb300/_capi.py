@@ -97,6 +97,14 @@ SIGNATURES = {
     "cvx_integrate_batch": (_i32, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(cvx_scan_desc), _i32, _vp]),
     "cvx_batch_error": (_i32, [_vp]),
     "cvx_batch_destroy": (None, [_vp]),
+    "cvx_point_features": (_i32, [_vp, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
+    "cvx_weight_model_create": (_i32, [_vp, ctypes.POINTER(_vp)]),
+    "cvx_weight_model_params": (_i32, [_vp, _vp, _vp, _vp]),
+    "cvx_weight_model_infer": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "cvx_weight_model_train_step": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, _vp]),
+    "cvx_weight_model_last": (_i32, [_vp, _vp, _vp, _vp]),
+    "cvx_weight_model_destroy": (None, [_vp]),
+    "cvx_training_targets": (_i32, [_vp, _vp, _i64, _vp, ctypes.POINTER(cvx_integrate_params), _vp, _vp, _vp]),
     "cvx_profile_start": (_i32, [_i64]),
     "cvx_profile_stop": (_i32, []),
     "cvx_profile_read": (_i32, [_i32, _vp, _vp, _vp]),
@@ -259,3 +267,71 @@ def cvx_profile_read() -> dict:
 
 def cvx_launch_count() -> int:
     return int(lib().cvx_launch_count())
+
+
+CVX_MLP_PARAMS = 1217
+
+
+def cvx_point_features(points, height: int, width: int, sensor: int, max_range: float, out, stream=None):
+    check(lib().cvx_point_features(_dev_ptr(points, "torch.float32", "points"), height, width, sensor,
+                                   float(max_range), _dev_ptr(out, "torch.float32", "features"),
+                                   _stream_handle(stream)), "cvx_point_features")
+
+
+def cvx_weight_model_create(init_params: np.ndarray) -> int:
+    p = np.ascontiguousarray(init_params, dtype=np.float32).reshape(CVX_MLP_PARAMS)
+    h = ctypes.c_void_p()
+    check(lib().cvx_weight_model_create(p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)),
+          "cvx_weight_model_create")
+    return h.value
+
+
+def cvx_weight_model_params(model: int, set_params=None, get=False, stream=None):
+    sp = None
+    if set_params is not None:
+        sp = np.ascontiguousarray(set_params, dtype=np.float32).reshape(CVX_MLP_PARAMS)
+    out = np.zeros(CVX_MLP_PARAMS, np.float32) if get else None
+    check(lib().cvx_weight_model_params(model, None if sp is None else sp.ctypes.data_as(ctypes.c_void_p),
+                                        None if out is None else out.ctypes.data_as(ctypes.c_void_p),
+                                        _stream_handle(stream)), "cvx_weight_model_params")
+    if sp is not None and not get:
+        import torch
+        torch.cuda.current_stream().synchronize()   # the host copy is read asynchronously
+    return out
+
+
+def cvx_weight_model_infer(model: int, features, weights_out, stream=None):
+    n = int(features.shape[0])
+    check(lib().cvx_weight_model_infer(model, _dev_ptr(features, "torch.float32", "features"), n,
+                                       _dev_ptr(weights_out, "torch.float32", "weights"), _stream_handle(stream)),
+          "cvx_weight_model_infer")
+
+
+def cvx_weight_model_train_step(model: int, features, e2, mask, lr: float, stream=None):
+    n = int(features.shape[0])
+    check(lib().cvx_weight_model_train_step(model, _dev_ptr(features, "torch.float32", "features"),
+                                            _dev_ptr(e2, "torch.float32", "e2"), _dev_ptr(mask, "torch.float32", "mask"),
+                                            n, float(lr), _stream_handle(stream)), "cvx_weight_model_train_step")
+
+
+def cvx_weight_model_last(model: int, stream=None):
+    g = np.zeros(CVX_MLP_PARAMS, np.float32)
+    loss = np.zeros(1, np.float32)
+    check(lib().cvx_weight_model_last(model, g.ctypes.data_as(ctypes.c_void_p), loss.ctypes.data_as(ctypes.c_void_p),
+                                      _stream_handle(stream)), "cvx_weight_model_last")
+    return g, float(loss[0])
+
+
+def cvx_weight_model_destroy(model: int) -> None:
+    if model:
+        lib().cvx_weight_model_destroy(model)
+
+
+def cvx_training_targets(clean_handle: int, points, T_sub_sensor, params, e2_out, mask_out, stream=None):
+    n = int(points.shape[0])
+    T = np.ascontiguousarray(T_sub_sensor, dtype=np.float32).reshape(12)
+    check(lib().cvx_training_targets(clean_handle, _dev_ptr(points, "torch.float32", "points") if n else None, n,
+                                     T.ctypes.data_as(ctypes.c_void_p), ctypes.byref(params),
+                                     _dev_ptr(e2_out, "torch.float32", "e2"),
+                                     _dev_ptr(mask_out, "torch.float32", "mask"), _stream_handle(stream)),
+          "cvx_training_targets")
