@@ -480,6 +480,8 @@ def run_ours(args):
         "gpu_launches_per_step_counted": launches_per_step,
         "clocks": clk,
     }
+    if not args.no_learned:
+        out["forms"]["learned_weight"] = learned_form(wl, pts, Ts, stream, args, ws, rmse32, ms32 / args.steps)
     if not args.no_batched:
         import scenegen as sg
         wl4 = sg.make_c4()
@@ -502,6 +504,83 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):
+    """Learned per-point weight on the multiroom workload: train the network
+    on three other seeded buildings (noisy vs noise-free fused TSDF targets),
+    then time features + inference + per-point-weight integration per frame,
+    and compare the SDF RMSE with the plain quadratic weight (gate)."""
+    import torch
+    import scenegen as sg
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import _capi, weights
+    sm = wl.submaps[0]
+    H, W = sm.scans[0].height, sm.scans[0].width
+    t0 = time.perf_counter()
+    F, E, M = [], [], []
+    for seed in (31, 32, 34):
+        noisy = sg.make_c2(seed=seed, n_frames=8, width=W, height=H)
+        clean = sg.make_c2(seed=seed, n_frames=8, width=W, height=H, noise=False)
+        f, e, m = weights.build_training_set(noisy.submaps[0].scans, clean.submaps[0].scans, sm.voxel_size,
+                                             sm.trunc, wl.max_range)
+        F.append(f), E.append(e), M.append(m)
+    F, E, M = torch.cat(F), torch.cat(E), torch.cat(M)
+    E, _ = weights.normalise_targets(E, M)
+    model = weights.WeightModel(seed=0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = weights.train(model, F, E, M, steps=1500, batch=65536, lr=3e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    N = sm.scans[0].points.shape[0]
+    feats = torch.empty((N, 3), dtype=torch.float32, device="cuda")
+    wbuf = torch.empty(N, dtype=torch.float32, device="cuda")
+    prm = cvx.integrate_params(cvx.CVX_W_PER_POINT, wl.dropoff, wl.min_range, wl.max_range, 0, H, W, args.ppc)
+    with torch.cuda.stream(stream):
+        sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, 0, max_blocks=args.max_blocks, stream=stream)
+
+    def step():
+        sub.reset(stream)
+        for f in range(len(Ts)):
+            _capi.cvx_point_features(pts[f], H, W, 0, wl.max_range, feats, stream)
+            _capi.cvx_weight_model_infer(model.handle, feats, wbuf, stream)
+            sub.integrate(pts[f], Ts[f], prm, wbuf, stream)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    keys, D, Wt = (t.cpu().numpy() for t in sub.extract(stream))
+    rmse_l = sdf_rmse(wl.scene, keys, D.astype(np.float64), Wt.astype(np.float64), sm.voxel_size, sm.trunc)
+    c = sub.counters()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        step()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            g.replay()
+        barrier(ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        e1.record(stream)
+        barrier(ws)
+    ms = max_over_ranks(e0.elapsed_time(e1), ws) / args.steps
+    _capi.cvx_profile_start(1 << 20)
+    step()
+    torch.cuda.synchronize()
+    _capi.cvx_profile_stop()
+    prof = _capi.cvx_profile_read()
+    sub.close()
+    model.close()
+    return {"points_per_s": sum_over_ranks(c["valid_points"], ws) / (ms / 1e3),
+            "ms_per_step": ms, "speedup_vs_fp32": ms_plain / ms, "sdf_rmse_m": rmse_l, "sdf_rmse_plain_quadratic_m": rmse_plain,
+            "gate_keeps_learned": bool(weights.gate(rmse_l, rmse_plain)),
+            "training": {"points": int(F.shape[0]), "steps": 1500, "batch": 65536,
+                         "loss_first50": float(np.mean(losses[:50])), "loss_last50": float(np.mean(losses[-50:])),
+                         "data_s": t1 - t0, "train_s": t2 - t1},
+            "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}}
 
 
 def run_lidar(args, ws, rank, peaks, peak_src):
@@ -601,6 +680,7 @@ def main():
     ap.add_argument("--workload", default="multiroom", choices=["multiroom", "room", "lidar"])
     ap.add_argument("--scans", type=int, default=2000, help="LiDAR scans (lidar workload)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form (multiroom)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-weight form (multiroom)")
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--ppc", type=int, default=0, help="points per CTA of the accumulation pass")
     ap.add_argument("--max-blocks", type=int, default=1 << 18)
