@@ -194,6 +194,14 @@ int32_t cvx_batch_error(cvx_batch* batch);
 
 void cvx_batch_destroy(cvx_batch* batch);
 
+/* Tracing of the batched kernel: with timing enabled, CTA 0 stamps the GPU
+ * global timer after each grid barrier; cvx_batch_phase_times() (synchronous)
+ * returns, for each wave of the last batch, the milliseconds of phase 1
+ * (tiles), phase 2 (merges) and phase 3 (bookkeeping), each including its
+ * barrier: ms[3 * wave + phase].  Returns the number of waves written. */
+cvx_status cvx_batch_timing(cvx_batch* batch, int32_t enable);
+int32_t cvx_batch_phase_times(cvx_batch* batch, double* ms, int32_t max_waves);
+
 /* ---- learned per-point weight (Sec. III-C weighting paragraph) ----
  * Features of an organised scan, one row of three per point (device float32
  * [height*width, 3]): f1 = |P| / max_range; f2 = theta / (pi/2) with theta the

@@ -97,6 +97,8 @@ SIGNATURES = {
     "cvx_integrate_batch": (_i32, [_vp, ctypes.POINTER(_vp), _i32, ctypes.POINTER(cvx_scan_desc), _i32, _vp]),
     "cvx_batch_error": (_i32, [_vp]),
     "cvx_batch_destroy": (None, [_vp]),
+    "cvx_batch_timing": (_i32, [_vp, _i32]),
+    "cvx_batch_phase_times": (_i32, [_vp, _vp, _i32]),
     "cvx_point_features": (_i32, [_vp, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "cvx_weight_model_create": (_i32, [_vp, ctypes.POINTER(_vp)]),
     "cvx_weight_model_params": (_i32, [_vp, _vp, _vp, _vp]),
@@ -196,6 +198,19 @@ def cvx_integrate_batch(batch: int, maps, scans, stream=None) -> None:
 
 def cvx_batch_error(batch: int) -> int:
     return int(lib().cvx_batch_error(batch))
+
+
+def cvx_batch_timing(batch: int, enable: bool) -> None:
+    check(lib().cvx_batch_timing(batch, int(enable)), "cvx_batch_timing")
+
+
+def cvx_batch_phase_times(batch: int, max_waves: int = 1 << 16) -> np.ndarray:
+    """[waves, 3] milliseconds of phase 1 (tiles), 2 (merge), 3 (bookkeeping)."""
+    out = np.zeros(3 * max_waves, np.float64)
+    n = lib().cvx_batch_phase_times(batch, out.ctypes.data_as(ctypes.c_void_p), max_waves)
+    if n < 0:
+        raise CovoxError(n, "cvx_batch_phase_times")
+    return out[:3 * n].reshape(n, 3)
 
 
 def cvx_batch_destroy(batch: int) -> None:

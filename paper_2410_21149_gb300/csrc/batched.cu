@@ -40,7 +40,18 @@ struct BatchDev {
   unsigned* bar_count;
   unsigned* bar_gen;
   int* err;
+  unsigned long long* phase_ns;   // [n_waves * 3 + 1] globaltimer stamps, or nullptr
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void stamp(const BatchDev& b, int slot) {
+  if (b.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) b.phase_ns[slot] = global_ns();
+}
 
 constexpr long long kBarrierSpin = 1ll << 24;   // ~1 s at the sleep below
 constexpr int kMaxWaveScans = 1024;
@@ -86,6 +97,7 @@ __global__ void __launch_bounds__(kTileThreads) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int nt_prefix[kMaxWaveScans + 1];
   const int tid = threadIdx.x;
+  stamp(b, 0);
   for (int w = 0; w < b.n_waves; ++w) {
     const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
     // phase 1: tiles of all scans of the wave
@@ -95,6 +107,7 @@ __global__ void __launch_bounds__(kTileThreads) batched_kernel(BatchDev b) {
       integrate_tile(b.maps[b.scan_map[s]], b.scans[s], t0 + t - b.tile_prefix[s], smem, b.scan_lb[s]);
     }
     if (!grid_barrier(b)) return;
+    stamp(b, 3 * w + 1);
     // phase 2: merge every touched block of every submap of the wave
     if (tid == 0) {
       int acc = 0;
@@ -120,6 +133,7 @@ __global__ void __launch_bounds__(kTileThreads) batched_kernel(BatchDev b) {
       if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
     }
     if (!grid_barrier(b)) return;
+    stamp(b, 3 * w + 2);
     // phase 3: per-submap bookkeeping of this frame
     if (blockIdx.x == 0) {
       for (int s = s0 + tid; s < s1; s += blockDim.x) {
@@ -132,6 +146,7 @@ __global__ void __launch_bounds__(kTileThreads) batched_kernel(BatchDev b) {
       }
     }
     if (!grid_barrier(b)) return;
+    stamp(b, 3 * w + 3);
   }
 }
 
@@ -147,6 +162,9 @@ struct cvx_batch {
   bool pending;
   int grid;           // persistent grid size (CTAs)
   int lb_max;
+  unsigned long long* phase_ns;   // [3 * max_scans + 1] when phase timing is on
+  bool timing;
+  int last_waves;
 };
 
 namespace {
@@ -201,6 +219,14 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
     return CVX_ERR_OOM;
   }
   b->lb_max = kMaxLocalBlocks;
+  if (cudaMalloc((void**)&b->phase_ns, sizeof(unsigned long long) * (3 * (size_t)max_scans + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->dev);
+    cudaFreeHost(b->host);
+    cudaFree(b->bar);
+    delete b;
+    return CVX_ERR_OOM;
+  }
   cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)tile_smem_bytes(kMaxLocalBlocks));
   int per_sm = 0;
@@ -221,8 +247,33 @@ void cvx_batch_destroy(cvx_batch* b) {
   cudaFree(b->dev);
   cudaFreeHost(b->host);
   cudaFree(b->bar);
+  cudaFree(b->phase_ns);
   cudaEventDestroy(b->copied);
   delete b;
+}
+
+cvx_status cvx_batch_timing(cvx_batch* b, int32_t enable) {
+  if (!b) return CVX_ERR_INVALID_ARG;
+  b->timing = enable != 0;
+  return CVX_OK;
+}
+
+int32_t cvx_batch_phase_times(cvx_batch* b, double* ms, int32_t max_waves) {
+  if (!b || !ms || max_waves <= 0) return CVX_ERR_INVALID_ARG;
+  const int nw = b->last_waves < max_waves ? b->last_waves : max_waves;
+  if (nw <= 0) return 0;
+  unsigned long long* t = new (std::nothrow) unsigned long long[3 * (size_t)nw + 1];
+  if (!t) return CVX_ERR_OOM;
+  if (cudaMemcpy(t, b->phase_ns, sizeof(unsigned long long) * (3 * (size_t)nw + 1), cudaMemcpyDeviceToHost) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    delete[] t;
+    return CVX_ERR_CUDA;
+  }
+  for (int w = 0; w < nw; ++w)
+    for (int p = 0; p < 3; ++p) ms[3 * w + p] = (double)(t[3 * w + p + 1] - t[3 * w + p]) * 1e-6;
+  delete[] t;
+  return nw;
 }
 
 cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_maps,
@@ -313,6 +364,8 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   bd.bar_count = b->bar;
   bd.bar_gen = b->bar + 1;
   bd.err = (int*)(b->bar + 2);
+  bd.phase_ns = b->timing ? b->phase_ns : nullptr;
+  b->last_waves = n_waves;
   if (cudaMemsetAsync(b->bar, 0, 16, st) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
