@@ -189,6 +189,11 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
 cvx_status cvx_integrate_batch(cvx_batch* batch, cvx_submap* const* maps, int32_t n_maps,
                                const cvx_scan_desc* scans, int32_t n_scans, void* stream);
 
+/* Tuning: cut every wave into chunks of at most max_scans_per_wave scans (0 =
+ * no limit).  Smaller waves keep each wave's per-scan sums resident in L2 at
+ * the cost of more grid barriers.  Results do not depend on it. */
+cvx_status cvx_batch_wave_limit(cvx_batch* batch, int32_t max_scans_per_wave);
+
 /* CVX_ERR_TIMEOUT if a barrier of the last batch gave up (synchronous). */
 int32_t cvx_batch_error(cvx_batch* batch);
 

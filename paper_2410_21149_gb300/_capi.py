@@ -98,6 +98,7 @@ SIGNATURES = {
     "cvx_batch_error": (_i32, [_vp]),
     "cvx_batch_destroy": (None, [_vp]),
     "cvx_batch_timing": (_i32, [_vp, _i32]),
+    "cvx_batch_wave_limit": (_i32, [_vp, _i32]),
     "cvx_batch_phase_times": (_i32, [_vp, _vp, _i32]),
     "cvx_point_features": (_i32, [_vp, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "cvx_weight_model_create": (_i32, [_vp, ctypes.POINTER(_vp)]),
@@ -198,6 +199,10 @@ def cvx_integrate_batch(batch: int, maps, scans, stream=None) -> None:
 
 def cvx_batch_error(batch: int) -> int:
     return int(lib().cvx_batch_error(batch))
+
+
+def cvx_batch_wave_limit(batch: int, max_scans_per_wave: int) -> None:
+    check(lib().cvx_batch_wave_limit(batch, int(max_scans_per_wave)), "cvx_batch_wave_limit")
 
 
 def cvx_batch_timing(batch: int, enable: bool) -> None:

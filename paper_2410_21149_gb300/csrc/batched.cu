@@ -93,7 +93,7 @@ __device__ __forceinline__ int find_scan(const int* prefix, int lo, int hi, int 
   return lo;
 }
 
-__global__ void __launch_bounds__(kTileThreads) batched_kernel(BatchDev b) {
+__global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int nt_prefix[kMaxWaveScans + 1];
   const int tid = threadIdx.x;
@@ -121,16 +121,31 @@ __global__ void __launch_bounds__(kTileThreads) batched_kernel(BatchDev b) {
     __syncthreads();
     const int nt_total = nt_prefix[s1 - s0];
     const int half = tid >> 7, sub = tid & (kMergeThreads - 1);
-    for (int j = 2 * blockIdx.x + half; j < nt_total; j += 2 * gridDim.x) {
+    // each half CTA merges two blocks at a time (loads of both in flight);
+    // the pair shares a submap when the second block still belongs to it
+    for (int j = 2 * (2 * blockIdx.x + half); j < nt_total; j += 4 * gridDim.x) {
       const int q = find_scan(nt_prefix, 0, s1 - s0, j);
       const SubmapDev& m = b.maps[b.scan_map[s0 + q]];
       const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
-      const int merged = m.storage == 0 ? merge_block<0>(m, j - nt_prefix[q], skip, sub)
-                                        : merge_block<1>(m, j - nt_prefix[q], skip, sub);
+      const int lj = j - nt_prefix[q];
+      const bool pair = j + 1 < nt_prefix[q + 1];
+      int merged = m.storage == 0 ? merge_two<0>(m, lj, pair ? lj + 1 : -1, skip, sub)
+                                  : merge_two<1>(m, lj, pair ? lj + 1 : -1, skip, sub);
       unsigned long long c = merged;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
       if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
+      if (!pair && j + 1 < nt_total) {   // the next block starts the next submap
+        const int q3 = find_scan(nt_prefix, 0, s1 - s0, j + 1);
+        const SubmapDev& m2 = b.maps[b.scan_map[s0 + q3]];
+        const bool skip2 = *((volatile int32_t*)&m2.st->frame_err) != 0;
+        merged = m2.storage == 0 ? merge_two<0>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub)
+                                 : merge_two<1>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub);
+        c = merged;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((tid & 31) == 0 && c) atomicAdd(&m2.st->voxels_merged, c);
+      }
     }
     if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 2);
@@ -165,6 +180,7 @@ struct cvx_batch {
   unsigned long long* phase_ns;   // [3 * max_scans + 1] when phase timing is on
   bool timing;
   int last_waves;
+  int wave_limit;     // most scans per wave (0: no limit)
 };
 
 namespace {
@@ -252,6 +268,12 @@ void cvx_batch_destroy(cvx_batch* b) {
   delete b;
 }
 
+cvx_status cvx_batch_wave_limit(cvx_batch* b, int32_t max_scans_per_wave) {
+  if (!b || max_scans_per_wave < 0) return CVX_ERR_INVALID_ARG;
+  b->wave_limit = max_scans_per_wave;
+  return CVX_OK;
+}
+
 cvx_status cvx_batch_timing(cvx_batch* b, int32_t enable) {
   if (!b) return CVX_ERR_INVALID_ARG;
   b->timing = enable != 0;
@@ -297,13 +319,28 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     if (v != CVX_OK) return v;
     if (d.n == 0) continue;
     rank[s] = per_map[d.submap]++;
-    n_waves = std::max(n_waves, rank[s] + 1);
     lb_max = std::max(lb_max, lbs[s]);
     order.push_back(s);
   }
   if (order.empty()) return CVX_OK;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return rank[a] < rank[c]; });
   const int n_run = (int)order.size();
+  // waves: the k-th scans of all submaps, cut into chunks of at most
+  // wave_limit scans (chunks of one rank are independent of each other)
+  {
+    int w = -1, prev = -1, in_wave = 0;
+    for (int k = 0; k < n_run; ++k) {
+      const int rk = rank[order[k]];
+      if (rk != prev || (b->wave_limit > 0 && in_wave >= b->wave_limit)) {
+        ++w;
+        in_wave = 0;
+        prev = rk;
+      }
+      rank[order[k]] = w;   // from here on: the wave index
+      ++in_wave;
+    }
+    n_waves = w + 1;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {

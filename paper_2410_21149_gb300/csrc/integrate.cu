@@ -44,7 +44,11 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
   const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
   const int tid = threadIdx.x;
   unsigned long long merged = 0;
-  for (int j = blockIdx.x; j < nt; j += gridDim.x) merged += merge_block<kStore>(m, j, skip, tid);
+  const int g = (int)gridDim.x;
+  for (int j = blockIdx.x; j < nt; j += 2 * g) {
+    const int j1 = j + g < nt ? j + g : -1;
+    merged += merge_two<kStore>(m, j, j1, skip, tid);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) merged += __shfl_xor_sync(0xffffffffu, merged, o);
   if ((tid & 31) == 0) red[tid >> 5] = merged;

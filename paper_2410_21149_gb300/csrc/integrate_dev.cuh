@@ -69,37 +69,50 @@ __device__ __forceinline__ int find_pool(const SubmapDev& m, unsigned long long 
   return p >= 0 ? p : -1;
 }
 
-// Point index of iteration k of this thread in tile `tile`, or -1.
-__device__ __forceinline__ long long tile_point(const ScanDev& sc, int tile, int k) {
-  const int t = threadIdx.x;
-  if (!sc.organised) {
-    const long long base = (long long)tile * sc.tile_w * sc.tile_h;
-    const long long end = min(base + (long long)sc.tile_w * sc.tile_h, sc.n);
-    const long long i = base + (long long)k * kTileThreads + t;
-    return i < end ? i : -1;
+// Points of one tile: iteration k of this thread gives a point index or -1.
+struct TilePoints {
+  long long base, end;   // unorganised: [base, end)
+  int x0, y0;            // organised: tile origin in pixels
+
+  __device__ __forceinline__ TilePoints(const ScanDev& sc, int tile) {
+    if (!sc.organised) {
+      base = (long long)tile * sc.tile_w * sc.tile_h;
+      end = min(base + (long long)sc.tile_w * sc.tile_h, sc.n);
+      x0 = y0 = 0;
+    } else {
+      base = end = 0;
+      x0 = (tile % sc.tiles_x) * sc.tile_w;
+      y0 = (tile / sc.tiles_x) * sc.tile_h;
+    }
   }
-  int x, y;
-  if (sc.tile_w == 32 && (sc.tile_h & 31) == 0) {
-    // lanes of a warp on an 8 x 4 grid spaced 4 x 8 pixels over a 32 x 32 chunk:
-    // neighbouring lanes rarely share a voxel, so shared atomics rarely collide
-    const int l = t & 31, w = t >> 5;
-    const int c = k & 3;   // 4 iterations of 8 warps fill the 4 x 8 cell
-    x = (l & 7) * 4 + (w & 3);
-    y = (k >> 2) * 32 + (l >> 3) * 8 + (w >> 2) * 4 + c;
-  } else if (sc.tile_w == 32) {   // lanes on an 8 x 4 grid of a 32 x 8 chunk
-    const int l = t & 31, w = t >> 5;
-    x = (l & 7) * 4 + (w & 3);
-    y = k * 8 + (l >> 3) * 2 + (w >> 2);
-  } else {
-    const int p = k * kTileThreads + t;
-    x = p % sc.tile_w;
-    y = p / sc.tile_w;
+
+  __device__ __forceinline__ long long point(const ScanDev& sc, int k) const {
+    const int t = threadIdx.x;
+    if (!sc.organised) {
+      const long long i = base + (long long)k * kTileThreads + t;
+      return i < end ? i : -1;
+    }
+    int x, y;
+    if (sc.tile_w == 32 && (sc.tile_h & 31) == 0) {
+      // lanes of a warp on an 8 x 4 grid spaced 4 x 8 pixels over a 32 x 32 chunk:
+      // neighbouring lanes rarely share a voxel, so shared atomics rarely collide
+      const int l = t & 31, w = t >> 5;
+      x = (l & 7) * 4 + (w & 3);
+      y = (k >> 2) * 32 + (l >> 3) * 8 + (w >> 2) * 4 + (k & 3);
+    } else if (sc.tile_w == 32) {   // lanes on an 8 x 4 grid of a 32 x 8 chunk
+      const int l = t & 31, w = t >> 5;
+      x = (l & 7) * 4 + (w & 3);
+      y = k * 8 + (l >> 3) * 2 + (w >> 2);
+    } else {
+      const int p = k * kTileThreads + t;
+      x = p % sc.tile_w;
+      y = p / sc.tile_w;
+    }
+    const int gx = x0 + x, gy = y0 + y;
+    if (gx >= sc.width || gy >= sc.height || y >= sc.tile_h) return -1;
+    return (long long)gy * sc.width + gx;
   }
-  const int gx = (tile % sc.tiles_x) * sc.tile_w + x;
-  const int gy = (tile / sc.tiles_x) * sc.tile_h + y;
-  if (gx >= sc.width || gy >= sc.height || y >= sc.tile_h) return -1;
-  return (long long)gy * sc.width + gx;
-}
+};
 
 __device__ __forceinline__ int tile_iters(const ScanDev& sc) {
   return (sc.tile_w * sc.tile_h + kTileThreads - 1) / kTileThreads;
@@ -116,16 +129,26 @@ __device__ __forceinline__ int tile_iters(const ScanDev& sc) {
 // Sec. III-D allocation phase) and the slots are flushed with vector atomics
 // into the blocks' per-scan accumulators.  A block that finds the map full is
 // activated on the spot and accumulated straight into global memory.
+__device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
+  return ((uint32_t)key ^ (uint32_t)(key >> 29)) * 0x9E3779B1u;
+}
+
+constexpr int kCache = 64;          // block -> pool cache entries per CTA
+constexpr int kCachePending = -2;
+
 struct TileSmem {
   unsigned long long* mkey;   // [lb] block key of each slot, kEmptyKey if free
   int* pool;                  // [lb]
   float* swd;                 // [lb * 512]
   float* sw;                  // [lb * 512]
   unsigned long long* red;    // [2 * warps]
+  unsigned long long* ckey;   // [kCache] block -> pool cache
+  int* cpool;                 // [kCache]
 };
 
 __host__ __device__ inline size_t tile_smem_bytes(int lb) {
-  return (size_t)lb * 8 + (size_t)lb * 4 + 2 * (kTileThreads / 32) * 8 + 16 + (size_t)lb * kVoxPerBlock * 8;
+  return (size_t)lb * 8 + (size_t)lb * 4 + 2 * (kTileThreads / 32) * 8 + 16 + (size_t)lb * kVoxPerBlock * 8 +
+         (size_t)kCache * 12 + 16;
 }
 
 __device__ inline TileSmem tile_smem(char* base, int lb) {
@@ -138,12 +161,39 @@ __device__ inline TileSmem tile_smem(char* base, int lb) {
   base += (size_t)lb * 8;
   t.red = reinterpret_cast<unsigned long long*>(base);
   base += 2 * (kTileThreads / 32) * 8;
+  t.ckey = reinterpret_cast<unsigned long long*>(base);
+  base += kCache * 8;
+  t.cpool = reinterpret_cast<int*>(base);
+  base += kCache * 4;
   t.pool = reinterpret_cast<int*>(base);
   return t;
 }
 
-__device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
-  return ((uint32_t)key ^ (uint32_t)(key >> 29)) * 0x9E3779B1u;
+// Pool index of a block through the CTA's block -> pool cache.  The first
+// thread to meet a block activates it and publishes the index; a thread that
+// finds the entry still pending activates it itself (activation is
+// idempotent), so nobody waits.
+__device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t, unsigned long long key) {
+  const uint32_t h = slot_hash(key) >> 26;
+  for (int p = 0; p < 8; ++p) {
+    const int q = (h + p) & (kCache - 1);
+    unsigned long long cur = *((volatile unsigned long long*)(t.ckey + q));
+    bool own = false;
+    if (cur == kEmptyKey) {
+      cur = atomicCAS(t.ckey + q, kEmptyKey, key);
+      own = cur == kEmptyKey;
+    }
+    if (own) {
+      const int pool = global_activate(m, key);
+      atomicExch(t.cpool + q, pool);
+      return pool;
+    }
+    if (cur == key) {
+      const int pool = *((volatile int*)(t.cpool + q));
+      return pool != kCachePending ? pool : global_activate(m, key);
+    }
+  }
+  return global_activate(m, key);
 }
 
 // Shared slot of a block in a map of lb (power of two) slots, or -1 if full.
@@ -162,13 +212,16 @@ __device__ __forceinline__ int local_slot(const TileSmem& t, int lb, unsigned lo
   return -1;
 }
 
-// lb == 0: no shared slots, every observation is a vector atomic on the
-// block's global per-scan sums (the L2 performs the float additions).
-__device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+template <bool kLocal, int kDrop>
+__device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
   const TileSmem t = tile_smem(smem, lb);
   const int tid = threadIdx.x;
-  for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
-  {
+  for (int q = tid; q < kCache; q += kTileThreads) {
+    t.ckey[q] = kEmptyKey;
+    t.cpool[q] = kCachePending;
+  }
+  if (kLocal) {
+    for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
     float4* z = reinterpret_cast<float4*>(t.swd);
     const int n4 = lb * kVoxPerBlock * 2 / 4;
     for (int q = tid; q < n4; q += kTileThreads) z[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -176,10 +229,11 @@ __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int
   __syncthreads();
 
   const float inv_drop = 1.0f / (m.trunc - m.vs);
-  unsigned long long n_obs = 0, n_valid = 0;
+  const TilePoints tp(sc, tile);
+  unsigned n_obs = 0, n_valid = 0;
   const int iters = tile_iters(sc);
   for (int k = 0; k < iters; ++k) {
-    const long long i = tile_point(sc, tile, k);
+    const long long i = tp.point(sc, k);
     if (i < 0) continue;
     Ray r;
     if (!make_ray(sc, i, r)) continue;
@@ -201,16 +255,16 @@ __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int
     const float dd2 = -(float)d.s[2] * m.vs * r.u[2];
     int l = local_index(d.v);
     unsigned long long key = pack_key(d.v[0] >> 3, d.v[1] >> 3, d.v[2] >> 3);
-    int slot = local_slot(t, lb, key);
-    int gpool = slot < 0 ? global_activate(m, key) : -1;
+    int slot = kLocal ? local_slot(t, lb, key) : -1;
+    int gpool = slot < 0 ? cached_pool(m, t, key) : -1;
     for (;;) {
       const float dc = fminf(fmaxf(dist, -m.trunc), m.trunc);
       float w = w0;
-      if (sc.dropoff != 0 && dc < -m.vs) {
+      if (kDrop != 0 && dc < -m.vs) {
         const float f = fmaxf((m.trunc + dc) * inv_drop, 0.0f);
-        w = sc.dropoff == 1 ? w * f : w * f * f;
+        w = kDrop == 1 ? w * f : w * f * f;
       }
-      if (slot >= 0) {
+      if (kLocal && slot >= 0) {
         atomicAdd(t.swd + slot * kVoxPerBlock + l, w * dc);
         atomicAdd(t.sw + slot * kVoxPerBlock + l, w);
       } else if (gpool >= 0) {
@@ -237,26 +291,28 @@ __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int
       l = (l & ~mask) | f;
       if (f == (sk > 0 ? 0 : mask)) {   // crossed into the neighbouring block
         key += sk > 0 ? (1ull << shift) : (0ull - (1ull << shift));
-        slot = local_slot(t, lb, key);
-        gpool = slot < 0 ? global_activate(m, key) : -1;
+        slot = kLocal ? local_slot(t, lb, key) : -1;
+        gpool = slot < 0 ? cached_pool(m, t, key) : -1;
       }
     }
   }
   __syncthreads();
-  // allocation: each distinct block of the tile is activated once
-  for (int q = tid; q < lb; q += kTileThreads) {
-    const unsigned long long key = t.mkey[q];
-    t.pool[q] = key == kEmptyKey ? -1 : global_activate(m, key);
-  }
-  __syncthreads();
-  // flush the tile's sums into the per-scan accumulators
-  for (int q = 0; q < lb; ++q) {
-    const int pool = t.pool[q];
-    if (pool < 0) continue;
-    float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
-    for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
-      const float w = t.sw[q * kVoxPerBlock + v];
-      if (w != 0.0f) atomicAdd(dst + v, make_float2(t.swd[q * kVoxPerBlock + v], w));
+  if (kLocal) {
+    // allocation: each distinct block of the tile's shared slots is activated once
+    for (int q = tid; q < lb; q += kTileThreads) {
+      const unsigned long long key = t.mkey[q];
+      t.pool[q] = key == kEmptyKey ? -1 : cached_pool(m, t, key);
+    }
+    __syncthreads();
+    // flush the tile's sums into the per-scan accumulators
+    for (int q = 0; q < lb; ++q) {
+      const int pool = t.pool[q];
+      if (pool < 0) continue;
+      float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
+      for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
+        const float w = t.sw[q * kVoxPerBlock + v];
+        if (w != 0.0f) atomicAdd(dst + v, make_float2(t.swd[q * kVoxPerBlock + v], w));
+      }
     }
   }
 #pragma unroll
@@ -279,6 +335,22 @@ __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int
     if (c) atomicAdd(&m.st->valid_pts, c);
   }
   __syncthreads();   // shared memory is reused by the caller's next tile
+}
+
+// lb > 0: per-voxel sums of up to lb blocks in shared memory, flushed once per
+// tile; lb == 0: every observation is a vector atomic on the block's global
+// per-scan sums (the L2 performs the float additions).  The accumulation and
+// drop-off modes are compile-time variants.
+__device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+  if (lb > 0) {
+    if (sc.dropoff == 0) integrate_tile_t<true, 0>(m, sc, tile, smem, lb);
+    else if (sc.dropoff == 1) integrate_tile_t<true, 1>(m, sc, tile, smem, lb);
+    else integrate_tile_t<true, 2>(m, sc, tile, smem, lb);
+  } else {
+    if (sc.dropoff == 0) integrate_tile_t<false, 0>(m, sc, tile, smem, lb);
+    else if (sc.dropoff == 1) integrate_tile_t<false, 1>(m, sc, tile, smem, lb);
+    else integrate_tile_t<false, 2>(m, sc, tile, smem, lb);
+  }
 }
 
 // ------------------------------------------------------------- merge
@@ -326,38 +398,71 @@ struct Vox4<1> {   // FP16 storage: D / trunc and W as IEEE half, FP32 arithmeti
   }
 };
 
-// Merge the sums of touched block j (kMergeThreads threads, this one is
-// `tid`); returns the number of voxels merged by this thread.
+// Merge the sums of touched blocks j0 and j1 (j1 < 0: none) with
+// kMergeThreads threads, this one being `tid` (4 voxels of each block).  All
+// loads of both blocks are issued before any result is used, so two blocks'
+// dependent chains overlap.  Returns the voxels merged by this thread.
 template <int kStore>
-__device__ __forceinline__ int merge_block(const SubmapDev& m, int j, bool skip, int tid) {
-  const int pool = m.touched[j];
-  float4* a = reinterpret_cast<float4*>(m.acc + (size_t)pool * kVoxPerBlock) + 2 * tid;
+__device__ __forceinline__ int merge_two(const SubmapDev& m, int j0, int j1, bool skip, int tid) {
+  const int p0 = m.touched[j0];
+  const int p1 = j1 >= 0 ? m.touched[j1] : -1;
+  float4* a = reinterpret_cast<float4*>(m.acc + (size_t)p0 * kVoxPerBlock) + 2 * tid;
+  float4* b = p1 >= 0 ? reinterpret_cast<float4*>(m.acc + (size_t)p1 * kVoxPerBlock) + 2 * tid : nullptr;
   const float4 a0 = a[0], a1 = a[1];
-  const float swd[4] = {a0.x, a0.z, a1.x, a1.z};
-  const float sw[4] = {a0.y, a0.w, a1.y, a1.w};
+  float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
+  if (b) {
+    b0 = b[0];
+    b1 = b[1];
+  }
+  const float swa[4] = {a0.x, a0.z, a1.x, a1.z}, wa[4] = {a0.y, a0.w, a1.y, a1.w};
+  const float swb[4] = {b0.x, b0.z, b1.x, b1.z}, wb[4] = {b0.y, b0.w, b1.y, b1.w};
+  const bool ta = (wa[0] != 0.f) | (wa[1] != 0.f) | (wa[2] != 0.f) | (wa[3] != 0.f);
+  const bool tb = (wb[0] != 0.f) | (wb[1] != 0.f) | (wb[2] != 0.f) | (wb[3] != 0.f);
+  const size_t ea = (size_t)p0 * kVoxPerBlock + 4 * tid, eb = (size_t)(p1 >= 0 ? p1 : 0) * kVoxPerBlock + 4 * tid;
+  float Da[4], Wa[4], Db[4], Wb[4];
+  if (ta && !skip) Vox4<kStore>::load(m, ea, Da, Wa);
+  if (tb && !skip) Vox4<kStore>::load(m, eb, Db, Wb);
   int merged = 0;
-  if ((sw[0] != 0.0f) | (sw[1] != 0.0f) | (sw[2] != 0.0f) | (sw[3] != 0.0f)) {
+  if (ta) {
     if (!skip) {
-      const size_t e = (size_t)pool * kVoxPerBlock + 4 * tid;
-      float D[4], W[4];
-      Vox4<kStore>::load(m, e, D, W);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (sw[q] != 0.0f) {
-          const float wn = W[q] + sw[q];
-          D[q] = (D[q] * W[q] + swd[q]) / wn;
-          W[q] = fminf(wn, m.max_w);
+      for (int q = 0; q < 4; ++q)
+        if (wa[q] != 0.0f) {
+          const float wn = Wa[q] + wa[q];
+          Da[q] = (Da[q] * Wa[q] + swa[q]) / wn;
+          Wa[q] = fminf(wn, m.max_w);
           ++merged;
         }
-      }
-      Vox4<kStore>::store(m, e, D, W);
+      Vox4<kStore>::store(m, ea, Da, Wa);
     }
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    a[0] = z;
-    a[1] = z;
+    a[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    a[1] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (tid == 0) m.touch[pool] = -1;
+  if (tb) {
+    if (!skip) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (wb[q] != 0.0f) {
+          const float wn = Wb[q] + wb[q];
+          Db[q] = (Db[q] * Wb[q] + swb[q]) / wn;
+          Wb[q] = fminf(wn, m.max_w);
+          ++merged;
+        }
+      Vox4<kStore>::store(m, eb, Db, Wb);
+    }
+    b[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    b[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (tid == 0) {
+    m.touch[p0] = -1;
+    if (p1 >= 0) m.touch[p1] = -1;
+  }
   return merged;
+}
+
+template <int kStore>
+__device__ __forceinline__ int merge_block(const SubmapDev& m, int j, bool skip, int tid) {
+  return merge_two<kStore>(m, j, -1, skip, tid);
 }
 
 }  // namespace covox
