@@ -265,12 +265,15 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
         return max_over_ranks(e0.elapsed_time(e1), ws) / steps
 
     ms_b = graph_time(step_batched)
-    # one eager step: counters, kernel time, status
+    # one eager step: counters, kernel time, per-wave phase times, status
     _capi.cvx_profile_start(1 << 20)
+    _capi.cvx_batch_timing(batch, True)
     step_batched()
     torch.cuda.synchronize()
     _capi.cvx_profile_stop()
+    _capi.cvx_batch_timing(batch, False)
     prof = _capi.cvx_profile_read()
+    phases = _capi.cvx_batch_phase_times(batch)
     assert _capi.cvx_batch_error(batch) == 0 and all(s.status() == 0 for s in subs)
     cnt = [s.counters() for s in subs]
     tot = {k: sum(c[k] for c in cnt) for k in cnt[0]}
@@ -287,7 +290,10 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
             "blocks_touched": tot["blocks_touched"], "blocks_allocated": tot["n_blocks"],
             "scans": len(items), "submaps": len(subs), "tuned": {"pts_per_cta": ppc, "local_blocks": lb},
             "batched_kernel_ms": kern_ms, "kernel_bytes": kbytes, "sdf_rmse_m": rmse,
-            "reset_and_other_ms": ms_b - kern_ms}
+            "reset_and_other_ms": ms_b - kern_ms,
+            "phases": {"waves": int(len(phases)), "tiles_ms": float(phases[:, 0].sum()),
+                       "merge_ms": float(phases[:, 1].sum()), "bookkeeping_ms": float(phases[:, 2].sum()),
+                       "per_wave_median_ms": [float(x) for x in np.median(phases, 0)]}}
 
 
 # -------------------------------------------------------------- our arm
@@ -627,7 +633,8 @@ def run_lidar(args, ws, rank, peaks, peak_src):
                      "algorithmic_bytes_per_launch": r["kernel_bytes"], "avg_launch_ms": r["batched_kernel_ms"]},
         "counts_per_step": {k: r[k] for k in ("points", "observations", "voxels_merged", "blocks_touched",
                                               "blocks_allocated")},
-        "autotuned": r["tuned"], "gpu_launches": (1 + r["submaps"]) * args.steps, "clocks": clk,
+        "autotuned": r["tuned"], "batched_phases": r["phases"],
+        "gpu_launches": (1 + r["submaps"]) * args.steps, "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
