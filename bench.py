@@ -315,9 +315,19 @@ def run_ours(args):
     host = torch.from_numpy(np.stack([s.points for s in sm.scans])).pin_memory()
     pts = host.cuda()
     Ts = [s.T_sub_sensor for s in sm.scans]
-    params = cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range,
-                                  sm.scans[0].sensor, sm.scans[0].height, sm.scans[0].width,
-                                  args.ppc)
+    sc0 = sm.scans[0]
+
+    def prm_of(ppc, lb):
+        return cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range, sc0.sensor,
+                                    sc0.height, sc0.width, ppc, lb)
+
+    if args.ppc == 0:   # launch shape from the autotuner (first 20 frames, cached per device)
+        from paper_2410_21149_gb300 import autotune
+        tuned = autotune.tune_scans(sm.voxel_size, sm.trunc, wl.max_weight, 0,
+                                    [(pts[f], Ts[f]) for f in range(min(20, len(Ts)))], prm_of,
+                                    max_blocks=args.max_blocks)
+        args.ppc, args.lb = tuned["pts_per_cta"], tuned["local_blocks"]
+    params = prm_of(args.ppc, args.lb)
     stream = torch.cuda.Stream()
     max_blocks = args.max_blocks
 
@@ -476,6 +486,7 @@ def run_ours(args):
         "config": {"workload": wl.name, "frames_per_step": F, "points_per_frame": N,
                    "voxel_size_m": sm.voxel_size, "trunc_m": sm.trunc, "weight": "quadratic+linear-dropoff",
                    "storage": "f32", "step": "clear submap + integrate all frames (CUDA graph replay)",
+                   "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb},
                    "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (F * N * 12 / 1e6),
                    "parallelism": f"replica x{ws} (one submap sequence per GPU)"},
         "voxel_updates_per_s": tot_obs / sec32,
@@ -554,7 +565,8 @@ def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):
     N = sm.scans[0].points.shape[0]
     feats = torch.empty((N, 3), dtype=torch.float32, device="cuda")
     wbuf = torch.empty(N, dtype=torch.float32, device="cuda")
-    prm = cvx.integrate_params(cvx.CVX_W_PER_POINT, wl.dropoff, wl.min_range, wl.max_range, 0, H, W, args.ppc)
+    prm = cvx.integrate_params(cvx.CVX_W_PER_POINT, wl.dropoff, wl.min_range, wl.max_range, 0, H, W, args.ppc,
+                               args.lb)
     with torch.cuda.stream(stream):
         sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, 0, max_blocks=args.max_blocks, stream=stream)
 
@@ -701,7 +713,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form (multiroom)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-weight form (multiroom)")
     ap.add_argument("--frames", type=int, default=200)
-    ap.add_argument("--ppc", type=int, default=0, help="points per CTA of the accumulation pass")
+    ap.add_argument("--ppc", type=int, default=0, help="points per CTA tile (0: autotuned)")
+    ap.add_argument("--lb", type=int, default=0, help="shared block slots per CTA (-1: global atomics)")
     ap.add_argument("--max-blocks", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
