@@ -95,7 +95,7 @@ typedef struct {
   int32_t pts_per_cta;   /* tuning: points per CTA tile (0 = default; organised scans use
                             32-pixel-wide tiles of pts_per_cta / 32 rows) */
   int32_t local_blocks;  /* tuning: shared-memory block slots per CTA: 0 = default (8), a
-                            power of two <= 32, or -1 = no shared slots (global atomics) */
+                            power of two <= 16, or -1 = no shared slots (global atomics) */
   int32_t reserved;      /* must be 0 */
 } cvx_integrate_params;
 

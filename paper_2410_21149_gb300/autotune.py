@@ -21,7 +21,7 @@ from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 from . import _capi
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (256, 8), (256, 16), (256, 4), (256, -1), (512, 8), (512, 16), (512, -1), (1024, 16), (1024, -1))
+    (256, 2), (256, 4), (256, 8), (256, -1), (512, 4), (512, 8), (512, -1), (1024, 4), (1024, 8), (1024, -1))
 
 _lock = threading.Lock()
 

@@ -136,26 +136,37 @@ __device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
 constexpr int kCache = 64;          // block -> pool cache entries per CTA
 constexpr int kCachePending = -2;
 
+// Shared per-voxel sums are exact 64-bit fixed point X = hi * 2^S + lo held
+// in two 32-bit words (lo unsigned, < 2^S per observation; hi signed), so
+// every update is two native 32-bit integer atomics, which the hardware
+// merges when lanes collide (float shared atomics retry instead).
 struct TileSmem {
   unsigned long long* mkey;   // [lb] block key of each slot, kEmptyKey if free
   int* pool;                  // [lb]
-  float* swd;                 // [lb * 512]
-  float* sw;                  // [lb * 512]
+  unsigned* lo_wd;            // [lb * 512]
+  int* hi_wd;                 // [lb * 512]
+  unsigned* lo_w;             // [lb * 512]
+  int* hi_w;                  // [lb * 512]
+  float* wmax;                // [warps] per-warp maxima of the tile's weights
   unsigned long long* red;    // [2 * warps]
   unsigned long long* ckey;   // [kCache] block -> pool cache
   int* cpool;                 // [kCache]
 };
 
 __host__ __device__ inline size_t tile_smem_bytes(int lb) {
-  return (size_t)lb * 8 + (size_t)lb * 4 + 2 * (kTileThreads / 32) * 8 + 16 + (size_t)lb * kVoxPerBlock * 8 +
-         (size_t)kCache * 12 + 16;
+  return (size_t)lb * 8 + (size_t)lb * 4 + 2 * (kTileThreads / 32) * 8 + 16 + (size_t)lb * kVoxPerBlock * 16 +
+         (size_t)kCache * 12 + 16 + (kTileThreads / 32) * 4 + 16;
 }
 
 __device__ inline TileSmem tile_smem(char* base, int lb) {
   TileSmem t;
-  t.swd = reinterpret_cast<float*>(base);
+  t.lo_wd = reinterpret_cast<unsigned*>(base);
   base += (size_t)lb * kVoxPerBlock * 4;
-  t.sw = reinterpret_cast<float*>(base);
+  t.hi_wd = reinterpret_cast<int*>(base);
+  base += (size_t)lb * kVoxPerBlock * 4;
+  t.lo_w = reinterpret_cast<unsigned*>(base);
+  base += (size_t)lb * kVoxPerBlock * 4;
+  t.hi_w = reinterpret_cast<int*>(base);
   base += (size_t)lb * kVoxPerBlock * 4;
   t.mkey = reinterpret_cast<unsigned long long*>(base);
   base += (size_t)lb * 8;
@@ -165,8 +176,43 @@ __device__ inline TileSmem tile_smem(char* base, int lb) {
   base += kCache * 8;
   t.cpool = reinterpret_cast<int*>(base);
   base += kCache * 4;
+  t.wmax = reinterpret_cast<float*>(base);
+  base += ((kTileThreads / 32) * 4 + 15) / 16 * 16;
   t.pool = reinterpret_cast<int*>(base);
   return t;
+}
+
+// Fixed-point format of a tile: value = X * 2^-F, X = hi * 2^S + lo.  With
+// n observations per voxel at most (a ray meets a voxel once, so n <= the
+// tile's points) the lo words never overflow when n * 2^S <= 2^32, and the hi
+// words never overflow when n * max|X| < 2^(31 + S); F is the largest scale
+// with max|X| = 2 * wmax * max(trunc, 1) * 2^F inside that bound.
+struct Fixed {
+  int S;
+  float scale, inv_scale;   // 2^F, 2^-F
+};
+
+__device__ __forceinline__ Fixed fixed_format(int tile_points, float wmax, float trunc) {
+  const int bn = 32 - __clz(max(tile_points, 2) - 1);           // ceil(log2 n)
+  Fixed f;
+  f.S = 32 - bn;
+  const float bound = 2.0f * fmaxf(wmax, 1e-30f) * fmaxf(trunc, 1.0f);
+  int e;
+  frexpf(bound, &e);                                             // bound < 2^e
+  const int F = min(max(31 + f.S - bn - 1 - e, -120), 120);      // n * 2^(F+e) < 2^(31+S); 2^F a normal float
+  f.scale = ldexpf(1.0f, F);
+  f.inv_scale = ldexpf(1.0f, -F);
+  return f;
+}
+
+__device__ __forceinline__ void fixed_add(unsigned* lo, int* hi, int S, long long X) {
+  atomicAdd(lo, (unsigned)(X & ((1ll << S) - 1)));
+  atomicAdd(hi, (int)(X >> S));
+}
+
+__device__ __forceinline__ float fixed_value(unsigned lo, int hi, int S, float inv_scale) {
+  const long long X = ((long long)hi << S) + (long long)lo;
+  return (float)((double)X * (double)inv_scale);
 }
 
 // Pool index of a block through the CTA's block -> pool cache.  The first
@@ -220,18 +266,47 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     t.ckey[q] = kEmptyKey;
     t.cpool[q] = kCachePending;
   }
+  const TilePoints tp(sc, tile);
+  const int iters = tile_iters(sc);
+  Fixed fx;
   if (kLocal) {
     for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
-    float4* z = reinterpret_cast<float4*>(t.swd);
-    const int n4 = lb * kVoxPerBlock * 2 / 4;
-    for (int q = tid; q < n4; q += kTileThreads) z[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint4* z = reinterpret_cast<uint4*>(t.lo_wd);
+    const int n4 = lb * kVoxPerBlock * 4 / 4;
+    for (int q = tid; q < n4; q += kTileThreads) z[q] = make_uint4(0u, 0u, 0u, 0u);
+    // the fixed-point scale bounds the tile's weights (a cheap pre-pass over
+    // its points; the constant weight is 1)
+    float wm = 1.0f;
+    if (sc.weight_mode != 0) {
+      wm = 0.0f;
+      for (int k = 0; k < iters; ++k) {
+        const long long i = tp.point(sc, k);
+        if (i < 0) continue;
+        float w0;
+        if (sc.weight_mode == 2) {
+          w0 = __ldg(sc.pw + i);
+        } else {
+          const float x = __ldg(sc.pts + 3 * i), y = __ldg(sc.pts + 3 * i + 1), z3 = __ldg(sc.pts + 3 * i + 2);
+          const float zz = sc.sensor == 0 ? z3 * z3 : x * x + y * y + z3 * z3;
+          w0 = 1.0f / zz;
+        }
+        if (isfinite(w0)) wm = fmaxf(wm, fabsf(w0));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+      if ((tid & 31) == 0) t.wmax[tid >> 5] = wm;
+    }
+    __syncthreads();
+    if (sc.weight_mode != 0) {
+      wm = 0.0f;
+      for (int w = 0; w < kTileThreads / 32; ++w) wm = fmaxf(wm, t.wmax[w]);
+    }
+    fx = fixed_format(iters * kTileThreads, wm, m.trunc);
   }
   __syncthreads();
 
   const float inv_drop = 1.0f / (m.trunc - m.vs);
-  const TilePoints tp(sc, tile);
   unsigned n_obs = 0, n_valid = 0;
-  const int iters = tile_iters(sc);
   for (int k = 0; k < iters; ++k) {
     const long long i = tp.point(sc, k);
     if (i < 0) continue;
@@ -265,8 +340,9 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
         w = kDrop == 1 ? w * f : w * f * f;
       }
       if (kLocal && slot >= 0) {
-        atomicAdd(t.swd + slot * kVoxPerBlock + l, w * dc);
-        atomicAdd(t.sw + slot * kVoxPerBlock + l, w);
+        const int e = slot * kVoxPerBlock + l;
+        fixed_add(t.lo_wd + e, t.hi_wd + e, fx.S, __float2ll_rn(w * dc * fx.scale));
+        fixed_add(t.lo_w + e, t.hi_w + e, fx.S, __float2ll_rn(w * fx.scale));
       } else if (gpool >= 0) {
         atomicAdd(m.acc + (size_t)gpool * kVoxPerBlock + l, make_float2(w * dc, w));
       }
@@ -310,8 +386,11 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
       if (pool < 0) continue;
       float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
       for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
-        const float w = t.sw[q * kVoxPerBlock + v];
-        if (w != 0.0f) atomicAdd(dst + v, make_float2(t.swd[q * kVoxPerBlock + v], w));
+        const int e = q * kVoxPerBlock + v;
+        if ((t.lo_w[e] | (unsigned)t.hi_w[e]) == 0u) continue;
+        const float w = fixed_value(t.lo_w[e], t.hi_w[e], fx.S, fx.inv_scale);
+        const float wd = fixed_value(t.lo_wd[e], t.hi_wd[e], fx.S, fx.inv_scale);
+        if (w != 0.0f) atomicAdd(dst + v, make_float2(wd, w));
       }
     }
   }

@@ -48,64 +48,88 @@ __device__ __forceinline__ bool pt_valid(const float* P, int sensor) {
   return isfinite(P[0]) && isfinite(P[1]) && isfinite(P[2]) && (sensor != 0 || P[2] > 0.0f);
 }
 
-__global__ void features_kernel(const float* __restrict__ pts, int H, int W, int sensor, float max_range,
-                                float* __restrict__ out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= H * W) return;
-  const int v = idx / W, u = idx % W;
-  const float* P = pts + 3 * (size_t)idx;
+// One CTA per 32 x 8 pixel tile; the tile and its 2-pixel halo (36 x 12
+// points) are staged in shared memory once, with each point's validity and
+// depth (z for a pinhole, range for a spherical sensor).
+constexpr int kFtW = 32, kFtH = 8, kHalo = 2;
+constexpr int kFsW = kFtW + 2 * kHalo, kFsH = kFtH + 2 * kHalo;
+
+__global__ void __launch_bounds__(kFtW * kFtH) features_kernel(const float* __restrict__ pts, int H, int W,
+                                                                 int sensor, float max_range,
+                                                                 float* __restrict__ out) {
+  __shared__ float sp[kFsH][kFsW][3];
+  __shared__ float sz[kFsH][kFsW];
+  __shared__ unsigned char sv[kFsH][kFsW];
+  const int tiles_x = (W + kFtW - 1) / kFtW;
+  const int x0 = (blockIdx.x % tiles_x) * kFtW - kHalo, y0 = (blockIdx.x / tiles_x) * kFtH - kHalo;
+  for (int q = threadIdx.x; q < kFsW * kFsH; q += blockDim.x) {
+    const int ly = q / kFsW, lx = q % kFsW, gx = x0 + lx, gy = y0 + ly;
+    float P0 = NAN, P1 = NAN, P2 = NAN;
+    if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+      const float* P = pts + 3 * ((size_t)gy * W + gx);
+      P0 = P[0]; P1 = P[1]; P2 = P[2];
+    }
+    const float Pv[3] = {P0, P1, P2};
+    const bool ok = pt_valid(Pv, sensor);
+    sp[ly][lx][0] = P0; sp[ly][lx][1] = P1; sp[ly][lx][2] = P2;
+    sv[ly][lx] = ok;
+    sz[ly][lx] = ok ? (sensor == 0 ? P2 : sqrtf(P0 * P0 + P1 * P1 + P2 * P2)) : 0.0f;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kFtW, ty = threadIdx.x / kFtW;
+  const int u = x0 + kHalo + tx, v = y0 + kHalo + ty;
+  if (u >= W || v >= H) return;
+  const int cx = tx + kHalo, cy = ty + kHalo;
   float f[3] = {0.f, 0.f, 0.f};
-  if (pt_valid(P, sensor)) {
+  if (sv[cy][cx]) {
+    const float* P = sp[cy][cx];
     const float r = sqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
     f[0] = r / max_range;
     float th = 0.0f;
-    if (u > 0 && u < W - 1 && v > 0 && v < H - 1) {
-      const float* L = pts + 3 * (size_t)(idx - 1);
-      const float* R = pts + 3 * (size_t)(idx + 1);
-      const float* U = pts + 3 * (size_t)(idx - W);
-      const float* Dn = pts + 3 * (size_t)(idx + W);
-      if (pt_valid(L, sensor) && pt_valid(R, sensor) && pt_valid(U, sensor) && pt_valid(Dn, sensor)) {
-        const float a0 = R[0] - L[0], a1 = R[1] - L[1], a2 = R[2] - L[2];
-        const float b0 = Dn[0] - U[0], b1 = Dn[1] - U[1], b2 = Dn[2] - U[2];
-        const float n0 = a1 * b2 - a2 * b1, n1 = a2 * b0 - a0 * b2, n2 = a0 * b1 - a1 * b0;
-        const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
-        if (nn > 0.0f) {
-          const float c = fminf(fabsf(n0 * P[0] + n1 * P[1] + n2 * P[2]) / (nn * r), 1.0f);
-          th = acosf(c);
-        }
-      }
+    if (u > 0 && u < W - 1 && v > 0 && v < H - 1 && sv[cy][cx - 1] && sv[cy][cx + 1] && sv[cy - 1][cx] &&
+        sv[cy + 1][cx]) {
+      const float* L = sp[cy][cx - 1];
+      const float* R = sp[cy][cx + 1];
+      const float* U = sp[cy - 1][cx];
+      const float* Dn = sp[cy + 1][cx];
+      const float a0 = R[0] - L[0], a1 = R[1] - L[1], a2 = R[2] - L[2];
+      const float b0 = Dn[0] - U[0], b1 = Dn[1] - U[1], b2 = Dn[2] - U[2];
+      const float n0 = a1 * b2 - a2 * b1, n1 = a2 * b0 - a0 * b2, n2 = a0 * b1 - a1 * b0;
+      const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+      if (nn > 0.0f) th = acosf(fminf(fabsf(n0 * P[0] + n1 * P[1] + n2 * P[2]) / (nn * r), 1.0f));
     }
     f[1] = th / 1.57079632679489662f;
-    // 5x5 window, clipped at the border, two-pass population variance
+    // 5x5 window (clipped at the image border: out-of-image points are invalid)
     float sum = 0.0f;
     int cnt = 0;
-    for (int y = max(v - 2, 0); y <= min(v + 2, H - 1); ++y)
-      for (int x = max(u - 2, 0); x <= min(u + 2, W - 1); ++x) {
-        const float* Q = pts + 3 * ((size_t)y * W + x);
-        if (pt_valid(Q, sensor)) {
-          sum += sensor == 0 ? Q[2] : sqrtf(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2]);
+#pragma unroll
+    for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+      for (int dx = -2; dx <= 2; ++dx)
+        if (sv[cy + dy][cx + dx]) {
+          sum += sz[cy + dy][cx + dx];
           ++cnt;
         }
-      }
     float var = 0.0f;
     if (cnt >= 3) {
       const float mu = sum / cnt;
       float ss = 0.0f;
-      for (int y = max(v - 2, 0); y <= min(v + 2, H - 1); ++y)
-        for (int x = max(u - 2, 0); x <= min(u + 2, W - 1); ++x) {
-          const float* Q = pts + 3 * ((size_t)y * W + x);
-          if (pt_valid(Q, sensor)) {
-            const float z = sensor == 0 ? Q[2] : sqrtf(Q[0] * Q[0] + Q[1] * Q[1] + Q[2] * Q[2]);
-            ss += (z - mu) * (z - mu);
+#pragma unroll
+      for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+        for (int dx = -2; dx <= 2; ++dx)
+          if (sv[cy + dy][cx + dx]) {
+            const float e = sz[cy + dy][cx + dx] - mu;
+            ss += e * e;
           }
-        }
       var = ss / cnt;
     }
     f[2] = logf(var + 1e-8f) / 10.0f;
   }
-  out[3 * (size_t)idx] = f[0];
-  out[3 * (size_t)idx + 1] = f[1];
-  out[3 * (size_t)idx + 2] = f[2];
+  const size_t idx = (size_t)v * W + u;
+  out[3 * idx] = f[0];
+  out[3 * idx + 1] = f[1];
+  out[3 * idx + 2] = f[2];
 }
 
 // ------------------------------------------------------- training targets
@@ -383,6 +407,94 @@ __global__ void __launch_bounds__(kThreads) mlp_kernel(const float* __restrict__
   }
 }
 
+// Inference only: 8 warps, each with the weight fragments of both GEMMs held
+// in registers across its tiles of 16 points; small shared staging.
+constexpr int kIWarps = 8;
+struct alignas(128) InferWarp {
+  __nv_bfloat16 xb[16 * kInPad];
+  __nv_bfloat16 h1b[16 * kH];
+  __nv_bfloat16 h2b[16 * kH];
+  float c[16 * kH];
+};
+struct alignas(128) InferSmem {
+  alignas(128) __nv_bfloat16 w1b[kH * kInPad];
+  __nv_bfloat16 w2b[kH * kH];
+  float b1[kH], b2[kH], w3[kH], b3;
+  alignas(128) InferWarp warp[kIWarps];
+};
+
+__global__ void __launch_bounds__(32 * kIWarps) mlp_infer_kernel(const float* __restrict__ params,
+                                                                  const float* __restrict__ x, long long n,
+                                                                  float* __restrict__ wout) {
+  __shared__ InferSmem S;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  InferWarp& ws = S.warp[wid];
+  for (int q = tid; q < kH * kInPad; q += blockDim.x) {
+    const int o = q / kInPad, k = q % kInPad;
+    S.w1b[q] = __float2bfloat16_rn(k < kIn ? params[kOW1 + o * kIn + k] : 0.0f);
+  }
+  for (int q = tid; q < kH * kH; q += blockDim.x) S.w2b[q] = __float2bfloat16_rn(params[kOW2 + q]);
+  if (tid < kH) {
+    S.b1[tid] = params[kOB1 + tid];
+    S.b2[tid] = params[kOB2 + tid];
+    S.w3[tid] = params[kOW3 + tid];
+  }
+  if (tid == 0) S.b3 = params[kOB3];
+  __syncthreads();
+  wm::fragment<wm::matrix_b, 16, 16, 16, __nv_bfloat16, wm::col_major> B1[2], B2[2][2];
+  for (int nt = 0; nt < 2; ++nt) {
+    wm::load_matrix_sync(B1[nt], S.w1b + nt * 16 * kInPad, kInPad);
+    for (int kt = 0; kt < 2; ++kt) wm::load_matrix_sync(B2[nt][kt], S.w2b + nt * 16 * kH + kt * 16, kH);
+  }
+  const long long tiles = (n + 15) / 16;
+  for (long long t = (long long)blockIdx.x * kIWarps + wid; t < tiles; t += (long long)gridDim.x * kIWarps) {
+    const long long p0 = t * 16;
+    for (int q = lane; q < 16 * kInPad; q += 32) {
+      const int pt = q / kInPad, k = q % kInPad;
+      const long long i = p0 + pt;
+      ws.xb[q] = __float2bfloat16_rn((k < kIn && i < n) ? x[3 * i + k] : 0.0f);
+    }
+    __syncwarp();
+    {
+      wm::fragment<wm::matrix_a, 16, 16, 16, __nv_bfloat16, wm::row_major> a;
+      wm::load_matrix_sync(a, ws.xb, kInPad);
+      for (int nt = 0; nt < 2; ++nt) {
+        wm::fragment<wm::accumulator, 16, 16, 16, float> c;
+        wm::fill_fragment(c, 0.0f);
+        wm::mma_sync(c, a, B1[nt], c);
+        wm::store_matrix_sync(ws.c + nt * 16, c, kH, wm::mem_row_major);
+      }
+    }
+    __syncwarp();
+    for (int q = lane; q < 16 * kH; q += 32) ws.h1b[q] = __float2bfloat16_rn(fmaxf(ws.c[q] + S.b1[q % kH], 0.0f));
+    __syncwarp();
+    for (int nt = 0; nt < 2; ++nt) {
+      wm::fragment<wm::accumulator, 16, 16, 16, float> c;
+      wm::fill_fragment(c, 0.0f);
+      for (int kt = 0; kt < 2; ++kt) {
+        wm::fragment<wm::matrix_a, 16, 16, 16, __nv_bfloat16, wm::row_major> a;
+        wm::load_matrix_sync(a, ws.h1b + kt * 16, kH);
+        wm::mma_sync(c, a, B2[nt][kt], c);
+      }
+      wm::store_matrix_sync(ws.c + nt * 16, c, kH, wm::mem_row_major);
+    }
+    __syncwarp();
+    for (int q = lane; q < 16 * kH; q += 32) ws.h2b[q] = __float2bfloat16_rn(fmaxf(ws.c[q] + S.b2[q % kH], 0.0f));
+    __syncwarp();
+    // layer 3: two lanes per point, 16 features each
+    {
+      const int pt = lane >> 1, half = lane & 1;
+      float o = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) o += S.w3[half * 16 + k] * __bfloat162float(ws.h2b[pt * kH + half * 16 + k]);
+      o += __shfl_xor_sync(0xffffffffu, o, 1);
+      const long long i = p0 + pt;
+      if (half == 0 && i < n) wout[i] = softplus_f(o + S.b3);
+    }
+    __syncwarp();
+  }
+}
+
 // Fixed-order sum of the CTA partials, mean over valid points, Adam.
 __global__ void adam_kernel(float* __restrict__ params, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ partial, int nparts, float lr, float b1, float b2,
@@ -480,9 +592,9 @@ cvx_status cvx_point_features(const float* points, int32_t height, int32_t width
   if (!points || !features || height <= 0 || width <= 0 || (sensor != 0 && sensor != 1) || !(max_range > 0))
     return CVX_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = height * width;
+  const int tiles = ((width + kFtW - 1) / kFtW) * ((height + kFtH - 1) / kFtH);
   COVOX_LAUNCH(kKFeatures, s,
-               features_kernel<<<(n + 255) / 256, 256, 0, s>>>(points, height, width, sensor, max_range, features));
+               features_kernel<<<tiles, kFtW * kFtH, 0, s>>>(points, height, width, sensor, max_range, features));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
 
@@ -492,10 +604,8 @@ cvx_status cvx_weight_model_infer(cvx_weight_model* w, const float* features, in
   if (n == 0) return CVX_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const long long tiles = (n + 15) / 16;
-  const int grid = (int)std::min<long long>((tiles + kWarps - 1) / kWarps, (long long)num_sms() * 8);
-  COVOX_LAUNCH(kKMlpFwd, s,
-               mlp_kernel<0><<<grid, kThreads, sizeof(MlpSmem), s>>>(w->params, features, nullptr, nullptr, n,
-                                                                     weights, nullptr));
+  const int grid = (int)std::min<long long>((tiles + kIWarps - 1) / kIWarps, (long long)num_sms() * 4);
+  COVOX_LAUNCH(kKMlpFwd, s, mlp_infer_kernel<<<grid, 32 * kIWarps, 0, s>>>(w->params, features, n, weights));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
 

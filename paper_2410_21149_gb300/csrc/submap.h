@@ -37,7 +37,7 @@ inline int num_sms() {
 }
 
 constexpr int kDefaultLocalBlocks = 8;
-constexpr int kMaxLocalBlocks = 32;
+constexpr int kMaxLocalBlocks = 16;   // 8 KB of fixed-point sums each
 
 // Validate one scan's arguments and fill its device descriptor (with the
 // tile layout).  Returns CVX_OK or CVX_ERR_INVALID_ARG; *lb gets the number
