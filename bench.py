@@ -205,15 +205,16 @@ def multi_rmse(wl, subs, storage):
     return float(np.sqrt(np.mean(np.concatenate(errs)))) if errs else None
 
 
-def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=True, tune_force=False):
+def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=True, tune_force=False,
+                pipelined=True):
     """Many submaps: one batched persistent launch per step (autotuned tile
     shape, CUDA graph), beside the same scans through the per-scan path."""
     import torch
     import paper_2410_21149_gb300 as cvx
     from paper_2410_21149_gb300 import _capi, autotune
     stream = torch.cuda.Stream()
-    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks)
-            for sm in wl.submaps]
+    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
+                       pipelined=pipelined) for sm in wl.submaps]
     handles = [s.handle for s in subs]
     items = []
     for m, sm in enumerate(wl.submaps):
@@ -230,7 +231,7 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
             s.reset(st)
 
     tuned = autotune.tune_batch(handles, [(m, p, T, None, prm(sc)) for m, p, T, sc in items],
-                                f"{wl.name}|st{storage}", reset=reset, force=tune_force)
+                                f"{wl.name}|st{storage}|p{int(pipelined)}", reset=reset, force=tune_force)
     ppc, lb = tuned["pts_per_cta"], tuned["local_blocks"]
     bscans = [(m, p, T, None, prm(sc, ppc, lb)) for m, p, T, sc in items]
     batch = _capi.cvx_batch_create(len(subs), len(bscans))
@@ -290,7 +291,7 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
             "blocks_touched": tot["blocks_touched"], "blocks_allocated": tot["n_blocks"],
             "scans": len(items), "submaps": len(subs), "tuned": {"pts_per_cta": ppc, "local_blocks": lb},
             "batched_kernel_ms": kern_ms, "kernel_bytes": kbytes, "sdf_rmse_m": rmse,
-            "reset_and_other_ms": ms_b - kern_ms,
+            "reset_and_other_ms": ms_b - kern_ms, "pipelined": pipelined,
             "phases": {"waves": int(len(phases)), "tiles_ms": float(phases[:, 0].sum()),
                        "merge_ms": float(phases[:, 1].sum()), "bookkeeping_ms": float(phases[:, 2].sum()),
                        "per_wave_median_ms": [float(x) for x in np.median(phases, 0)]}}

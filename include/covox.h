@@ -71,6 +71,11 @@ typedef enum { CVX_SENSOR_PINHOLE = 0, CVX_SENSOR_SPHERICAL = 1 } cvx_sensor;
 typedef void* (*cvx_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*cvx_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 
+/* A pipelined submap holds a second set of per-scan sums and touched-block
+ * list, so that a batched launch can merge one scan of the submap while it
+ * accumulates the next one (same results; twice the per-scan memory). */
+#define CVX_SUBMAP_PIPELINED 1
+
 typedef struct {
   float voxel_size;      /* metres, > 0 */
   float trunc;           /* truncation distance, metres, > 0 */
@@ -78,7 +83,7 @@ typedef struct {
   int32_t storage;       /* cvx_storage */
   int64_t max_blocks;    /* block pool capacity (blocks of 512 voxels) */
   int64_t hash_slots;    /* hash table slots, a power of two >= 2 * max_blocks advised */
-  int64_t reserved;      /* must be 0 */
+  int64_t flags;         /* 0, or CVX_SUBMAP_PIPELINED */
   cvx_alloc_fn alloc;
   cvx_free_fn free;
   void* alloc_ctx;
@@ -203,7 +208,10 @@ void cvx_batch_destroy(cvx_batch* batch);
  * global timer after each grid barrier; cvx_batch_phase_times() (synchronous)
  * returns, for each wave of the last batch, the milliseconds of phase 1
  * (tiles), phase 2 (merges) and phase 3 (bookkeeping), each including its
- * barrier: ms[3 * wave + phase].  Returns the number of waves written. */
+ * barrier: ms[3 * wave + phase].  When every submap of the batch is
+ * pipelined, the entries are per step instead (n_waves + 1 steps): phase 1 =
+ * tiles of wave w together with the merges of wave w - 1, phase 2 = the
+ * bookkeeping of wave w - 1, phase 3 = 0.  Returns the entries written. */
 cvx_status cvx_batch_timing(cvx_batch* batch, int32_t enable);
 int32_t cvx_batch_phase_times(cvx_batch* batch, double* ms, int32_t max_waves);
 

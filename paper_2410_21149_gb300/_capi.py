@@ -23,6 +23,7 @@ CVX_STORE_F32, CVX_STORE_F16 = 0, 1
 CVX_W_CONST, CVX_W_QUADRATIC, CVX_W_PER_POINT = 0, 1, 2
 CVX_DROP_NONE, CVX_DROP_LINEAR, CVX_DROP_QUADRATIC = 0, 1, 2
 CVX_SENSOR_PINHOLE, CVX_SENSOR_SPHERICAL = 0, 1
+CVX_SUBMAP_PIPELINED = 1
 
 STATUS_NAMES = {0: "CVX_OK", -1: "CVX_ERR_INVALID_ARG", -2: "CVX_ERR_OOM", -3: "CVX_ERR_CAPACITY",
                 -4: "CVX_ERR_KEY_RANGE", -5: "CVX_ERR_TIMEOUT", -6: "CVX_ERR_CUDA"}
@@ -42,7 +43,7 @@ class cvx_submap_params(ctypes.Structure):
     _fields_ = [("voxel_size", ctypes.c_float), ("trunc", ctypes.c_float),
                 ("max_weight", ctypes.c_float), ("storage", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int64), ("hash_slots", ctypes.c_int64),
-                ("reserved", ctypes.c_int64), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("flags", ctypes.c_int64), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
 
 

@@ -30,18 +30,23 @@ using namespace covox;
 namespace {
 
 struct BatchDev {
-  const SubmapDev* maps;   // [n_maps]
+  const SubmapDev* maps;   // [n_maps] views, or [2 * n_maps] (parity views) when pipelined
   const ScanDev* scans;    // [n_scans] in wave order
   const int* scan_map;     // [n_scans] submap of each scan
   const int* scan_lb;      // [n_scans] shared block slots
   const int* tile_prefix;  // [n_scans + 1] tiles before each scan (wave order)
   const int* wave_begin;   // [n_waves + 1] first scan of each wave
   int n_waves;
+  int pipelined;           // 1: wave w uses per-scan set w & 1 and merges overlap the next tiles
   unsigned* bar_count;
   unsigned* bar_gen;
   int* err;
   unsigned long long* phase_ns;   // [n_waves * 3 + 1] globaltimer stamps, or nullptr
 };
+
+__device__ __forceinline__ const SubmapDev& view(const BatchDev& b, int map, int wave) {
+  return b.pipelined ? b.maps[2 * map + (wave & 1)] : b.maps[map];
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -93,74 +98,131 @@ __device__ __forceinline__ int find_scan(const int* prefix, int lo, int hi, int 
   return lo;
 }
 
+// Merge work of wave w: every touched block of every submap of the wave, in
+// pairs per half CTA (loads of both blocks in flight).  item = pair index.
+// One item = 4 consecutive blocks (2 per half CTA); items first_item,
+// first_item + step, ... (single: only the first).
+__device__ void merge_wave(const BatchDev& b, int w, const int* nt_prefix, int first_item, int step, bool single) {
+  const int tid = threadIdx.x;
+  const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
+  const int nt_total = nt_prefix[s1 - s0];
+  const int half = tid >> 7, sub = tid & (kMergeThreads - 1);
+  for (int item = first_item;; item += step) {
+    const int j = 4 * item + 2 * half;
+    if (j >= nt_total) break;
+    const int q = find_scan(nt_prefix, 0, s1 - s0, j);
+    const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
+    const bool skip = *((volatile int32_t*)m.frame_err) != 0;
+    const int lj = j - nt_prefix[q];
+    const bool pair = j + 1 < nt_prefix[q + 1];
+    int merged = m.storage == 0 ? merge_two<0>(m, lj, pair ? lj + 1 : -1, skip, sub)
+                                : merge_two<1>(m, lj, pair ? lj + 1 : -1, skip, sub);
+    unsigned long long c = merged;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
+    if (!pair && j + 1 < nt_total) {   // the next block starts the next submap
+      const int q3 = find_scan(nt_prefix, 0, s1 - s0, j + 1);
+      const SubmapDev& m2 = view(b, b.scan_map[s0 + q3], w);
+      const bool skip2 = *((volatile int32_t*)m2.frame_err) != 0;
+      merged = m2.storage == 0 ? merge_two<0>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub)
+                               : merge_two<1>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub);
+      c = merged;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if ((tid & 31) == 0 && c) atomicAdd(&m2.st->voxels_merged, c);
+    }
+    if (single) break;
+  }
+}
+
+// touched-block counts of wave w's scans (thread 0), prefix sums in nt_prefix
+__device__ void wave_touched(const BatchDev& b, int w, int* nt_prefix) {
+  if (threadIdx.x == 0) {
+    const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
+    int acc = 0;
+    for (int s = s0; s < s1; ++s) {
+      nt_prefix[s - s0] = acc;
+      const SubmapDev& m = view(b, b.scan_map[s], w);
+      acc += min(*((volatile int32_t*)m.n_touched), m.max_blocks);
+    }
+    nt_prefix[s1 - s0] = acc;
+  }
+  __syncthreads();
+}
+
+// per-submap bookkeeping of wave w's frames (CTA 0)
+__device__ void wave_bookkeeping(const BatchDev& b, int w, const int* nt_prefix) {
+  if (blockIdx.x != 0) return;
+  const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
+  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+    const SubmapDev& m = view(b, b.scan_map[s], w);
+    State* st = m.st;
+    st->blocks_touched += (unsigned long long)(nt_prefix[s - s0 + 1] - nt_prefix[s - s0]);
+    st->frames += 1;
+    st->sticky_err |= *m.frame_err;
+    *m.frame_err = 0;
+    *m.n_touched = 0;
+  }
+}
+
 __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int nt_prefix[kMaxWaveScans + 1];
-  const int tid = threadIdx.x;
   stamp(b, 0);
-  for (int w = 0; w < b.n_waves; ++w) {
-    const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
-    // phase 1: tiles of all scans of the wave
-    const int t0 = b.tile_prefix[s0], total = b.tile_prefix[s1] - t0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
-      const int s = find_scan(b.tile_prefix, s0, s1, t0 + t);
-      integrate_tile(b.maps[b.scan_map[s]], b.scans[s], t0 + t - b.tile_prefix[s], smem, b.scan_lb[s]);
+  if (!b.pipelined) {
+    for (int w = 0; w < b.n_waves; ++w) {
+      const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
+      // phase 1: tiles of all scans of the wave
+      const int t0 = b.tile_prefix[s0], total = b.tile_prefix[s1] - t0;
+      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int s = find_scan(b.tile_prefix, s0, s1, t0 + t);
+        integrate_tile(view(b, b.scan_map[s], w), b.scans[s], t0 + t - b.tile_prefix[s], smem, b.scan_lb[s]);
+      }
+      if (!grid_barrier(b)) return;
+      stamp(b, 3 * w + 1);
+      // phase 2: merge every touched block of every submap of the wave
+      wave_touched(b, w, nt_prefix);
+      merge_wave(b, w, nt_prefix, blockIdx.x, gridDim.x, false);
+      if (!grid_barrier(b)) return;
+      stamp(b, 3 * w + 2);
+      // phase 3: per-submap bookkeeping of this frame
+      wave_bookkeeping(b, w, nt_prefix);
+      if (!grid_barrier(b)) return;
+      stamp(b, 3 * w + 3);
+    }
+    return;
+  }
+  // pipelined: step w runs the tiles of wave w and the merges of wave w - 1
+  // (different per-scan sets; tiles never read D or W), then the bookkeeping
+  // of wave w - 1 frees its set for wave w + 1.
+  for (int w = 0; w <= b.n_waves; ++w) {
+    int n_tiles = 0, t0 = 0, s0 = 0, s1 = 0;
+    if (w < b.n_waves) {
+      s0 = b.wave_begin[w];
+      s1 = b.wave_begin[w + 1];
+      t0 = b.tile_prefix[s0];
+      n_tiles = b.tile_prefix[s1] - t0;
+    }
+    int n_pairs = 0;
+    if (w > 0) {
+      wave_touched(b, w - 1, nt_prefix);
+      n_pairs = (nt_prefix[b.wave_begin[w] - b.wave_begin[w - 1]] + 3) / 4;   // 4 blocks per CTA item
+    }
+    const int items = n_tiles + n_pairs;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      if (it < n_tiles) {
+        const int s = find_scan(b.tile_prefix, s0, s1, t0 + it);
+        integrate_tile(view(b, b.scan_map[s], w), b.scans[s], t0 + it - b.tile_prefix[s], smem, b.scan_lb[s]);
+      } else {
+        merge_wave(b, w - 1, nt_prefix, it - n_tiles, 1, true);   // one item: 4 blocks
+      }
     }
     if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 1);
-    // phase 2: merge every touched block of every submap of the wave
-    if (tid == 0) {
-      int acc = 0;
-      for (int s = s0; s < s1; ++s) {
-        nt_prefix[s - s0] = acc;
-        const SubmapDev& m = b.maps[b.scan_map[s]];
-        acc += min(*((volatile int32_t*)&m.st->n_touched), m.max_blocks);
-      }
-      nt_prefix[s1 - s0] = acc;
-    }
-    __syncthreads();
-    const int nt_total = nt_prefix[s1 - s0];
-    const int half = tid >> 7, sub = tid & (kMergeThreads - 1);
-    // each half CTA merges two blocks at a time (loads of both in flight);
-    // the pair shares a submap when the second block still belongs to it
-    for (int j = 2 * (2 * blockIdx.x + half); j < nt_total; j += 4 * gridDim.x) {
-      const int q = find_scan(nt_prefix, 0, s1 - s0, j);
-      const SubmapDev& m = b.maps[b.scan_map[s0 + q]];
-      const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
-      const int lj = j - nt_prefix[q];
-      const bool pair = j + 1 < nt_prefix[q + 1];
-      int merged = m.storage == 0 ? merge_two<0>(m, lj, pair ? lj + 1 : -1, skip, sub)
-                                  : merge_two<1>(m, lj, pair ? lj + 1 : -1, skip, sub);
-      unsigned long long c = merged;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
-      if (!pair && j + 1 < nt_total) {   // the next block starts the next submap
-        const int q3 = find_scan(nt_prefix, 0, s1 - s0, j + 1);
-        const SubmapDev& m2 = b.maps[b.scan_map[s0 + q3]];
-        const bool skip2 = *((volatile int32_t*)&m2.st->frame_err) != 0;
-        merged = m2.storage == 0 ? merge_two<0>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub)
-                                 : merge_two<1>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub);
-        c = merged;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if ((tid & 31) == 0 && c) atomicAdd(&m2.st->voxels_merged, c);
-      }
-    }
+    if (w > 0) wave_bookkeeping(b, w - 1, nt_prefix);
     if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 2);
-    // phase 3: per-submap bookkeeping of this frame
-    if (blockIdx.x == 0) {
-      for (int s = s0 + tid; s < s1; s += blockDim.x) {
-        State* st = b.maps[b.scan_map[s]].st;
-        st->blocks_touched += (unsigned long long)(nt_prefix[s - s0 + 1] - nt_prefix[s - s0]);
-        st->frames += 1;
-        st->sticky_err |= st->frame_err;
-        st->frame_err = 0;
-        st->n_touched = 0;
-      }
-    }
-    if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 3);
   }
 }
@@ -195,7 +257,7 @@ Layout layout(int max_maps, int max_scans) {
   Layout L;
   size_t o = 0;
   L.maps = o;
-  o = align16(o + sizeof(SubmapDev) * max_maps);
+  o = align16(o + sizeof(SubmapDev) * 2 * max_maps);
   L.scans = o;
   o = align16(o + sizeof(ScanDev) * max_scans);
   L.scan_map = o;
@@ -235,7 +297,7 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
     return CVX_ERR_OOM;
   }
   b->lb_max = kMaxLocalBlocks;
-  if (cudaMalloc((void**)&b->phase_ns, sizeof(unsigned long long) * (3 * (size_t)max_scans + 1)) != cudaSuccess) {
+  if (cudaMalloc((void**)&b->phase_ns, sizeof(unsigned long long) * (3 * (size_t)max_scans + 8)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->dev);
     cudaFreeHost(b->host);
@@ -364,7 +426,16 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   int* hlb = (int*)(h + L.scan_lb);
   int* htp = (int*)(h + L.tile_prefix);
   int* hwb = (int*)(h + L.wave_begin);
-  for (int q = 0; q < n_maps; ++q) hm[q] = maps[q]->dev;
+  bool pipelined = true;
+  for (int q = 0; q < n_maps; ++q) pipelined = pipelined && maps[q]->pipelined;
+  for (int q = 0; q < n_maps; ++q) {
+    if (pipelined) {
+      hm[2 * q] = maps[q]->dev;
+      hm[2 * q + 1] = maps[q]->dev_b;
+    } else {
+      hm[q] = maps[q]->dev;
+    }
+  }
   int tiles = 0, wave = -1;
   for (int k = 0; k < n_run; ++k) {
     const int s = order[k];
@@ -398,11 +469,12 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   bd.tile_prefix = (const int*)(d + L.tile_prefix);
   bd.wave_begin = (const int*)(d + L.wave_begin);
   bd.n_waves = n_waves;
+  bd.pipelined = pipelined ? 1 : 0;
   bd.bar_count = b->bar;
   bd.bar_gen = b->bar + 1;
   bd.err = (int*)(b->bar + 2);
   bd.phase_ns = b->timing ? b->phase_ns : nullptr;
-  b->last_waves = n_waves;
+  b->last_waves = pipelined ? n_waves + 1 : n_waves;   // pipelined: steps (tiles of w + merges of w - 1)
   if (cudaMemsetAsync(b->bar, 0, 16, st) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_CUDA;

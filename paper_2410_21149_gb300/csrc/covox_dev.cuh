@@ -22,7 +22,9 @@ struct State {
   int32_t frame_err;    // error bits of the current scan
   int32_t sticky_err;   // OR of all scans' error bits
   uint32_t ticket;      // last-CTA detection of the merge pass
-  int32_t pad[3];
+  int32_t n_touched_b;  // second per-scan set of a pipelined submap
+  int32_t frame_err_b;
+  int32_t pad;
   unsigned long long frames, valid_pts, obs, voxels_merged, blocks_touched;
 };
 
@@ -37,6 +39,8 @@ struct SubmapDev {
   float2* acc;                // [max_blocks,512] per-scan sums (sum w d, sum w), zero between scans
   int32_t* touched;           // [max_blocks] pool index of each block touched by the scan
   State* st;
+  int32_t* n_touched;         // per-scan counters of this view (&st->n_touched or _b)
+  int32_t* frame_err;
   uint32_t slot_mask;
   int32_t max_probe;
   int32_t max_blocks;

@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(kTileThreads) integrate_kernel(SubmapDev m, Sc
 template <int kStore>
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
   __shared__ unsigned long long red[kMergeThreads / 32];
-  const int nt = min(*((volatile int32_t*)&m.st->n_touched), m.max_blocks);
-  const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
+  const int nt = min(*((volatile int32_t*)m.n_touched), m.max_blocks);
+  const bool skip = *((volatile int32_t*)m.frame_err) != 0;
   const int tid = threadIdx.x;
   unsigned long long merged = 0;
   const int g = (int)gridDim.x;
@@ -64,9 +64,9 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
       State* st = m.st;
       st->blocks_touched += (unsigned long long)nt;
       st->frames += 1;
-      st->sticky_err |= st->frame_err;
-      st->frame_err = 0;
-      st->n_touched = 0;
+      st->sticky_err |= *m.frame_err;
+      *m.frame_err = 0;
+      *m.n_touched = 0;
       st->ticket = 0;
     }
   }
@@ -131,7 +131,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   if (p->max_blocks <= 0 || p->max_blocks > (1ll << 25)) return CVX_ERR_INVALID_ARG;
   if (p->hash_slots < 2 || (p->hash_slots & (p->hash_slots - 1)) || p->hash_slots > (1ll << 31))
     return CVX_ERR_INVALID_ARG;
-  if (p->reserved != 0) return CVX_ERR_INVALID_ARG;
+  if (p->flags & ~(int64_t)CVX_SUBMAP_PIPELINED) return CVX_ERR_INVALID_ARG;
   if (p->storage == CVX_STORE_F16 && p->max_weight > 65504.0f) return CVX_ERR_INVALID_ARG;
   if ((p->alloc == nullptr) != (p->free == nullptr)) return CVX_ERR_INVALID_ARG;
 
@@ -150,7 +150,16 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
   d.touched = (int32_t*)sub_alloc(m, nb * 4);
   d.st = (State*)sub_alloc(m, sizeof(State));
-  if (m->n_allocs != 9) {
+  int expect = 9;
+  m->pipelined = (p->flags & CVX_SUBMAP_PIPELINED) != 0;
+  SubmapDev& db = m->dev_b;
+  if (m->pipelined) {   // second per-scan set: sums, touch map, touched list
+    db.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
+    db.touch = (int32_t*)sub_alloc(m, nb * 4);
+    db.touched = (int32_t*)sub_alloc(m, nb * 4);
+    expect = 12;
+  }
+  if (m->n_allocs != expect) {
     sub_free_all(m);
     delete m;
     return CVX_ERR_OOM;
@@ -160,10 +169,23 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.max_blocks = (int)nb;
   d.max_touched = (int)nb;
   d.storage = p->storage;
+  d.n_touched = &d.st->n_touched;
+  d.frame_err = &d.st->frame_err;
   d.vs = p->voxel_size;
   d.inv_vs = 1.0f / p->voxel_size;
   d.trunc = p->trunc;
   d.max_w = p->max_weight;
+  if (m->pipelined) {
+    float2* acc_b = db.acc;
+    int32_t* touch_b = db.touch;
+    int32_t* touched_b = db.touched;
+    db = d;
+    db.acc = acc_b;
+    db.touch = touch_b;
+    db.touched = touched_b;
+    db.n_touched = &d.st->n_touched_b;
+    db.frame_err = &d.st->frame_err_b;
+  }
   cudaStream_t s = (cudaStream_t)p->stream;
   m->last_stream = s;
   cudaMemsetAsync(d.keys, 0xff, slots * 8, s);
@@ -173,6 +195,10 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   cudaMemsetAsync(d.W, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
   cudaMemsetAsync(d.st, 0, sizeof(State), s);
+  if (m->pipelined) {
+    cudaMemsetAsync(db.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
+    cudaMemsetAsync(db.touch, 0xff, nb * 4, s);
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     sub_free_all(m);
@@ -279,7 +305,7 @@ cvx_status cvx_submap_status(cvx_submap* map) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
-  return status_from_bits(st.sticky_err | st.frame_err);
+  return status_from_bits(st.sticky_err | st.frame_err | st.frame_err_b);
 }
 
 void cvx_destroy(cvx_submap* map) {

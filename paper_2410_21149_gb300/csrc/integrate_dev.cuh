@@ -26,14 +26,14 @@ __device__ inline int global_activate(const SubmapDev& m, unsigned long long key
   bool inserted;
   const int s = hash_activate(m, key, &inserted);
   if (s < 0) {
-    atomicOr(&m.st->frame_err, kErrCapacity);
+    atomicOr(m.frame_err, kErrCapacity);
     return -1;
   }
   int pool;
   if (inserted) {
     pool = atomicAdd(&m.st->n_blocks, 1);
     if (pool >= m.max_blocks) {
-      atomicOr(&m.st->frame_err, kErrCapacity);
+      atomicOr(m.frame_err, kErrCapacity);
       atomicExch(m.vals + s, kMapDead);
       return -1;
     }
@@ -48,13 +48,13 @@ __device__ inline int global_activate(const SubmapDev& m, unsigned long long key
       pool = *((volatile int32_t*)(m.vals + s));
     }
     if (pool == -1) {
-      atomicOr(&m.st->frame_err, kErrTimeout);
+      atomicOr(m.frame_err, kErrTimeout);
       return -1;
     }
     if (pool < 0) return -1;
   }
   if (*((volatile int32_t*)(m.touch + pool)) == -1 && atomicCAS(m.touch + pool, -1, -2) == -1) {
-    const int j = atomicAdd(&m.st->n_touched, 1);   // j < max_blocks: each block once per scan
+    const int j = atomicAdd(m.n_touched, 1);   // j < max_blocks: each block once per scan
     m.touched[j] = pool;
     atomicExch(m.touch + pool, j);
   }
@@ -314,7 +314,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     if (!make_ray(sc, i, r)) continue;
     float A[3], B[3];
     if (!band(r, m.trunc, m.inv_vs, A, B)) {
-      atomicOr(&m.st->frame_err, kErrKeyRange);
+      atomicOr(m.frame_err, kErrKeyRange);
       continue;
     }
     ++n_valid;

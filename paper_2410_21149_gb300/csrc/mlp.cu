@@ -446,14 +446,24 @@ __global__ void __launch_bounds__(32 * kIWarps) mlp_infer_kernel(const float* __
     wm::load_matrix_sync(B1[nt], S.w1b + nt * 16 * kInPad, kInPad);
     for (int kt = 0; kt < 2; ++kt) wm::load_matrix_sync(B2[nt][kt], S.w2b + nt * 16 * kH + kt * 16, kH);
   }
+  // padding columns of the input tile stay zero; each tile writes its 48 values
+  for (int q = lane; q < 16 * kInPad; q += 32) ws.xb[q] = __float2bfloat16_rn(0.0f);
+  __syncwarp();
   const long long tiles = (n + 15) / 16;
-  for (long long t = (long long)blockIdx.x * kIWarps + wid; t < tiles; t += (long long)gridDim.x * kIWarps) {
+  long long t = (long long)blockIdx.x * kIWarps + wid;
+  // the next tile's inputs are loaded (coalesced, 48 floats) while this one runs
+  float nx0 = 0.f, nx1 = 0.f;
+  auto load = [&](long long tt) {
+    const long long b = tt * 48;
+    nx0 = (tt < tiles && b + lane < 3 * n) ? __ldg(x + b + lane) : 0.0f;
+    nx1 = (tt < tiles && lane < 16 && b + 32 + lane < 3 * n) ? __ldg(x + b + 32 + lane) : 0.0f;
+  };
+  load(t);
+  for (; t < tiles; t += (long long)gridDim.x * kIWarps) {
     const long long p0 = t * 16;
-    for (int q = lane; q < 16 * kInPad; q += 32) {
-      const int pt = q / kInPad, k = q % kInPad;
-      const long long i = p0 + pt;
-      ws.xb[q] = __float2bfloat16_rn((k < kIn && i < n) ? x[3 * i + k] : 0.0f);
-    }
+    ws.xb[(lane / 3) * kInPad + lane % 3] = __float2bfloat16_rn(nx0);
+    if (lane < 16) ws.xb[((32 + lane) / 3) * kInPad + (32 + lane) % 3] = __float2bfloat16_rn(nx1);
+    load(t + (long long)gridDim.x * kIWarps);
     __syncwarp();
     {
       wm::fragment<wm::matrix_a, 16, 16, 16, __nv_bfloat16, wm::row_major> a;

@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(kTileThreads) integrate_static_kernel(SubmapDe
 
 __global__ void __launch_bounds__(kMergeThreads) merge_static_kernel(SubmapDev m) {
   __shared__ unsigned long long red[kMergeThreads / 32];
-  const int nt = min(*((volatile int32_t*)&m.st->n_touched), m.max_blocks);
-  const bool skip = *((volatile int32_t*)&m.st->frame_err) != 0;
+  const int nt = min(*((volatile int32_t*)m.n_touched), m.max_blocks);
+  const bool skip = *((volatile int32_t*)m.frame_err) != 0;
   unsigned long long merged = 0;
   for (int j = blockIdx.x; j < nt; j += gridDim.x) merged += merge_block<0>(m, j, skip, threadIdx.x);
 #pragma unroll
@@ -95,9 +95,9 @@ __global__ void __launch_bounds__(kMergeThreads) merge_static_kernel(SubmapDev m
       State* st = m.st;
       st->blocks_touched += (unsigned long long)nt;
       st->frames += 1;
-      st->sticky_err |= st->frame_err;
-      st->frame_err = 0;
-      st->n_touched = 0;
+      st->sticky_err |= *m.frame_err;
+      *m.frame_err = 0;
+      *m.n_touched = 0;
       st->ticket = 0;
     }
   }
@@ -142,6 +142,8 @@ extern "C" cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, co
   m.D = view->dist;
   m.W = view->weight;
   m.st = (State*)view->state;
+  m.n_touched = &m.st->n_touched;
+  m.frame_err = &m.st->frame_err;
   unsigned char* base = (unsigned char*)scratch;
   m.acc = (float2*)base;
   m.touch = (int32_t*)(base + kAccBytes);

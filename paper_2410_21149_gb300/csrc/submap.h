@@ -14,12 +14,14 @@
 struct cvx_submap {
   cvx_submap_params p;
   covox::SubmapDev dev;
+  covox::SubmapDev dev_b;   // the second per-scan set of a pipelined submap
+  bool pipelined;
   size_t bytes_per_vox;
   cudaStream_t last_stream;
   struct Alloc {
     void* ptr;
     size_t bytes;
-  } allocs[12];
+  } allocs[16];
   int n_allocs;
 };
 

@@ -91,14 +91,15 @@ def compare(gpu, orc, d_tol, w_rel=1e-4, w_floor=1e-6, fp16_trunc=None):
             "voxels": int(both.sum()), "blocks": int(len(ko))}
 
 
-def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=False, **over):
+def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=False, pipelined=False,
+                    wave_limit=0, **over):
     """Integrate all submaps of the workload with one cvx_integrate_batch call
     (scans of a submap are frames in order).  Returns the run_gpu tuple list."""
     import torch
     import paper_2410_21149_gb300 as cvx
     from paper_2410_21149_gb300 import _capi
     storages = storages or [wl.storage] * len(wl.submaps)
-    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, st, max_blocks=max_blocks)
+    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, st, max_blocks=max_blocks, pipelined=pipelined)
             for sm, st in zip(wl.submaps, storages)]
     keep = []
     scans = []
@@ -113,6 +114,7 @@ def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=Fa
                 scans.append((m, pts, sc.T_sub_sensor, None, int_params(wl, sc, **over)))
         k += 1
     batch = _capi.cvx_batch_create(len(subs), len(scans))
+    _capi.cvx_batch_wave_limit(batch, wave_limit)
     handles = [s.handle for s in subs]
     if graph:
         s = torch.cuda.Stream()

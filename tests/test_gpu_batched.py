@@ -21,9 +21,12 @@ def mixed():
     return sg.make_c4(n_submaps=6, max_scans=4, depth_wh=(160, 120), lidar_rc=(16, 256))
 
 
-def test_batched_mixed_fp32_fp16_vs_oracle(mixed):
+@pytest.mark.parametrize("pipelined,wave_limit", [(False, 0), (True, 0), (True, 2)])
+def test_batched_mixed_fp32_fp16_vs_oracle(mixed, pipelined, wave_limit):
+    """Mixed storage; plain and pipelined waves (merges of one wave overlap the
+    next wave's tiles), and waves cut into chunks of two scans."""
     storages = [m % 2 for m in range(len(mixed.submaps))]
-    g = run_gpu_batched(mixed, storages)
+    g = run_gpu_batched(mixed, storages, pipelined=pipelined, wave_limit=wave_limit)
     for m, (a, st) in enumerate(zip(g, storages)):
         sm = mixed.submaps[m]
         sub = sg.Workload(mixed.name, [sm], mixed.max_weight, mixed.weight_mode, mixed.dropoff,
@@ -49,8 +52,9 @@ def test_batched_equals_per_scan_path():
         compare(gb[m], (*sort_blocks(gs[0], gs[1], gs[2]), {}), 1e-5)
 
 
-def test_batched_graph_capture_replay(mixed):
-    g = run_gpu_batched(mixed, graph=True)
+@pytest.mark.parametrize("pipelined", [False, True])
+def test_batched_graph_capture_replay(mixed, pipelined):
+    g = run_gpu_batched(mixed, graph=True, pipelined=pipelined)
     e = run_gpu_batched(mixed)
     for a, b in zip(g, e):
         compare(a, (*sort_blocks(b[0], b[1], b[2]), {}), 1e-3 * 0.6, fp16_trunc=0.6)
