@@ -166,6 +166,7 @@ __device__ void wave_bookkeeping(const BatchDev& b, int w, const int* nt_prefix)
   }
 }
 
+template <int kVariant>
 __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int nt_prefix[kMaxWaveScans + 1];
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
       const int t0 = b.tile_prefix[s0], total = b.tile_prefix[s1] - t0;
       for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int s = find_scan(b.tile_prefix, s0, s1, t0 + t);
-        integrate_tile(view(b, b.scan_map[s], w), b.scans[s], t0 + t - b.tile_prefix[s], smem, b.scan_lb[s]);
+        integrate_tile_v<kVariant>(view(b, b.scan_map[s], w), b.scans[s], t0 + t - b.tile_prefix[s], smem,
+                                   b.scan_lb[s]);
       }
       if (!grid_barrier(b)) return;
       stamp(b, 3 * w + 1);
@@ -213,7 +215,8 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
       if (it < n_tiles) {
         const int s = find_scan(b.tile_prefix, s0, s1, t0 + it);
-        integrate_tile(view(b, b.scan_map[s], w), b.scans[s], t0 + it - b.tile_prefix[s], smem, b.scan_lb[s]);
+        integrate_tile_v<kVariant>(view(b, b.scan_map[s], w), b.scans[s], t0 + it - b.tile_prefix[s], smem,
+                                   b.scan_lb[s]);
       } else {
         merge_wave(b, w - 1, nt_prefix, it - n_tiles, 1, true);   // one item: 4 blocks
       }
@@ -226,6 +229,10 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
     stamp(b, 3 * w + 3);
   }
 }
+
+using BatchedFn = void (*)(BatchDev);
+const BatchedFn kBatched[7] = {batched_kernel<-1>, batched_kernel<0>, batched_kernel<1>, batched_kernel<2>,
+                               batched_kernel<3>, batched_kernel<4>, batched_kernel<5>};
 
 }  // namespace
 
@@ -305,10 +312,11 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
     delete b;
     return CVX_ERR_OOM;
   }
-  cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)tile_smem_bytes(kMaxLocalBlocks));
+  for (int v = 0; v < 7; ++v)
+    cudaFuncSetAttribute((const void*)kBatched[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tile_smem_bytes(kMaxLocalBlocks));
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kTileThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kBatched[0], kTileThreads,
                                                     tile_smem_bytes(kDefaultLocalBlocks)) != cudaSuccess ||
       per_sm <= 0) {
     cudaGetLastError();
@@ -479,8 +487,15 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
+  // one variant for every scan: a kernel holding only that code
+  int variant = -2;
+  for (int k = 0; k < n_run; ++k) {
+    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff);
+    variant = variant == -2 ? v : (variant == v ? v : -1);
+  }
+  const BatchedFn kern = kBatched[variant + 1];
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kTileThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kTileThreads,
                                                     tile_smem_bytes(lb_max)) != cudaSuccess ||
       per_sm <= 0) {
     cudaGetLastError();
@@ -490,7 +505,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   void* args[] = {&bd};
   cudaError_t e;
   COVOX_LAUNCH(kKBatched, st,
-               e = cudaLaunchCooperativeKernel((void*)batched_kernel, dim3(grid), dim3(kTileThreads), args,
+               e = cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kTileThreads), args,
                                                tile_smem_bytes(lb_max), st));
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -32,10 +32,15 @@ using namespace covox;
 
 namespace {
 
+template <int kVariant>
 __global__ void __launch_bounds__(kTileThreads) integrate_kernel(SubmapDev m, ScanDev sc, int lb) {
   extern __shared__ __align__(16) char smem[];
-  integrate_tile(m, sc, blockIdx.x, smem, lb);
+  integrate_tile_v<kVariant>(m, sc, blockIdx.x, smem, lb);
 }
+
+using IntegrateFn = void (*)(SubmapDev, ScanDev, int);
+const IntegrateFn kIntegrate[6] = {integrate_kernel<0>, integrate_kernel<1>, integrate_kernel<2>,
+                                   integrate_kernel<3>, integrate_kernel<4>, integrate_kernel<5>};
 
 template <int kStore>
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
@@ -222,11 +227,13 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
   const size_t smem = tile_smem_bytes(lb);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(integrate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)tile_smem_bytes(kMaxLocalBlocks));
+    for (int v = 0; v < 6; ++v)
+      cudaFuncSetAttribute((const void*)kIntegrate[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tile_smem_bytes(kMaxLocalBlocks));
     attr_set = true;
   }
-  COVOX_LAUNCH(kKAccum, s, integrate_kernel<<<sc.n_tiles, kTileThreads, smem, s>>>(map->dev, sc, lb));
+  const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff)];
+  COVOX_LAUNCH(kKAccum, s, fn<<<sc.n_tiles, kTileThreads, smem, s>>>(map->dev, sc, lb));
   const int grid = std::min<int>(map->dev.max_blocks, num_sms() * 2);
   if (map->p.storage == CVX_STORE_F32)
     COVOX_LAUNCH(kKMerge, s, merge_kernel<0><<<grid, kMergeThreads, 0, s>>>(map->dev));

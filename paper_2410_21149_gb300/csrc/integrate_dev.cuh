@@ -432,6 +432,17 @@ __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int
   }
 }
 
+// Variant index of a scan: accumulation mode x drop-off (0..5), so a launch
+// whose scans share one variant runs a kernel holding only that code.
+__host__ __device__ inline int tile_variant(int lb, int dropoff) { return (lb > 0 ? 3 : 0) + dropoff; }
+
+template <int kVariant>
+__device__ __forceinline__ void integrate_tile_v(const SubmapDev& m, const ScanDev& sc, int tile, char* smem,
+                                                 int lb) {
+  if (kVariant < 0) integrate_tile(m, sc, tile, smem, lb);
+  else integrate_tile_t<(kVariant >= 3), (kVariant % 3)>(m, sc, tile, smem, lb);
+}
+
 // ------------------------------------------------------------- merge
 constexpr int kMergeThreads = 128;   // 4 voxels per thread
 
