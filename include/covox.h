@@ -72,8 +72,15 @@ typedef void* (*cvx_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*cvx_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 
 /* A pipelined submap holds a second set of per-scan sums and touched-block
- * list, so that a batched launch can merge one scan of the submap while it
- * accumulates the next one (same results; twice the per-scan memory). */
+ * list, so that the merge of one scan overlaps the accumulation of the next
+ * (same results; twice the per-scan memory).  In a batched launch the merges
+ * of wave k overlap the tiles of wave k + 1.  On the per-scan path each
+ * cvx_integrate_scan() launches one kernel that accumulates its scan and
+ * merges the scan of the previous call; the last scan stays pending until
+ * cvx_flush_submap(), cvx_extract_blocks(), cvx_submap_counters(),
+ * cvx_reset_submap() (which drops it) or a batched launch merges it.  Which
+ * set is in use lives on the device, so recorded CUDA graphs replay
+ * correctly. */
 #define CVX_SUBMAP_PIPELINED 1
 
 typedef struct {
@@ -141,14 +148,24 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
 cvx_status cvx_extract_blocks(cvx_submap* map, int64_t capacity, int32_t* keys, void* dist,
                               void* weight, int64_t* n_out, void* stream);
 
-/* Clear all blocks and counters (asynchronous, no host synchronisation). */
+/* Clear all blocks and counters (asynchronous, no host synchronisation).  A
+ * scan still pending in a pipelined submap is dropped. */
 cvx_status cvx_reset_submap(cvx_submap* map, void* stream);
+
+/* Pipelined submap: merge the scan the last cvx_integrate_scan() left
+ * pending, asynchronously on `stream` (one kernel; nothing when no scan is
+ * pending on the device).  Other submaps: no-op.  Coalescing the per-scan
+ * merge with the next scan's accumulation is this library's scheduling; the
+ * paper merges every frame before the next one (Sec. III-D), which is the
+ * result this reproduces. */
+cvx_status cvx_flush_submap(cvx_submap* map, void* stream);
 
 /* Sticky device error word as a status (CVX_OK if no error).  Synchronises the
  * stream of the last call on this submap. */
 cvx_status cvx_submap_status(cvx_submap* map);
 
-/* Cumulative counters (synchronises like cvx_submap_status). */
+/* Cumulative counters (synchronises like cvx_submap_status; merges a
+ * pending scan first). */
 cvx_status cvx_submap_counters(cvx_submap* map, cvx_counters* out);
 
 /* Free the submap and everything it allocated (synchronises its stream). */

@@ -85,6 +85,10 @@ class Submap:
     def reset(self, stream=None) -> None:
         _capi.cvx_reset_submap(self.handle, stream)
 
+    def flush(self, stream=None) -> None:
+        """Merge the scan a pipelined submap left pending (no-op otherwise)."""
+        _capi.cvx_flush_submap(self.handle, stream)
+
     def status(self) -> int:
         return _capi.cvx_submap_status(self.handle)
 

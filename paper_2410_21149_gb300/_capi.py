@@ -90,6 +90,7 @@ SIGNATURES = {
     "cvx_extract_blocks": (_i32, [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64), _vp]),
     "cvx_reset_submap": (_i32, [_vp, _vp]),
     "cvx_submap_status": (_i32, [_vp]),
+    "cvx_flush_submap": (_i32, [_vp, _vp]),
     "cvx_submap_counters": (_i32, [_vp, ctypes.POINTER(cvx_counters)]),
     "cvx_destroy": (None, [_vp]),
     "cvx_integrate_scan_noalloc": (_i32, [ctypes.POINTER(cvx_submap_view), _vp, _i64, _vp, _vp,
@@ -245,6 +246,10 @@ def cvx_extract_blocks(handle: int, capacity: int, keys, dist, weight, stream=No
 
 def cvx_reset_submap(handle: int, stream=None) -> None:
     check(lib().cvx_reset_submap(handle, _stream_handle(stream)), "cvx_reset_submap")
+
+
+def cvx_flush_submap(handle: int, stream=None) -> None:
+    check(lib().cvx_flush_submap(handle, _stream_handle(stream)), "cvx_flush_submap")
 
 
 def cvx_submap_status(handle: int) -> int:

@@ -467,7 +467,11 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     }
     b->pending = true;
   }
-  for (int q = 0; q < n_maps; ++q) maps[q]->last_stream = st;
+  for (int q = 0; q < n_maps; ++q) {
+    maps[q]->last_stream = st;
+    // a scan left pending by the pipelined per-scan path is merged first
+    if (flush_pending(maps[q], st, false) != CVX_OK) return CVX_ERR_CUDA;
+  }
   char* d = (char*)b->dev;
   BatchDev bd;
   bd.maps = (const SubmapDev*)(d + L.maps);

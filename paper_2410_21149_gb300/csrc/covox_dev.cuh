@@ -24,6 +24,8 @@ struct State {
   uint32_t ticket;      // last-CTA detection of the merge pass
   int32_t n_touched_b;  // second per-scan set of a pipelined submap
   int32_t frame_err_b;
+  int32_t parity;       // pipelined per-scan path: set the next scan accumulates into
+  int32_t pending;      // pipelined per-scan path: set parity ^ 1 holds an unmerged scan
   int32_t pad;
   unsigned long long frames, valid_pts, obs, voxels_merged, blocks_touched;
 };

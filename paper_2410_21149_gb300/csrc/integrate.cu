@@ -12,7 +12,11 @@
 //   merge_kernel     : one CTA per touched block: merge into D and W with
 //                      coalesced vector loads and stores; the last CTA resets
 //                      the per-scan state.  One owner per block: no write races.
-// The device functions both kernels use live in integrate_dev.cuh so that the
+// A submap created with CVX_SUBMAP_PIPELINED runs one kernel per scan
+// instead (integrate_pipelined_kernel): the merges of the previous scan share
+// the launch with this scan's tiles, and flush_kernel merges the last scan
+// before anything reads D and W.
+// The device functions all kernels use live in integrate_dev.cuh so that the
 // persistent batched kernel runs exactly the same arithmetic.
 #include <cuda_runtime.h>
 
@@ -44,9 +48,31 @@ const IntegrateFn kIntegrate[6] = {integrate_kernel<0>, integrate_kernel<1>, int
 
 template <int kStore>
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
+  __shared__ int head[2];
   __shared__ unsigned long long red[kMergeThreads / 32];
-  const int nt = min(*((volatile int32_t*)m.n_touched), m.max_blocks);
-  const bool skip = *((volatile int32_t*)m.frame_err) != 0;
+  if (threadIdx.x == 0) {
+    // Read the scan's touched-block count and error bits, then take a ticket
+    // (the fence orders the reads first; nothing is in flight yet).  The CTA
+    // drawing the last ticket knows every CTA has read them and closes the
+    // frame at once; the others merge from the values they read.
+    const int nt = min(*((volatile int32_t*)m.n_touched), m.max_blocks);
+    const int fe = *((volatile int32_t*)m.frame_err);
+    head[0] = nt;
+    head[1] = fe;
+    __threadfence();
+    if (atomicAdd(&m.st->ticket, 1u) == gridDim.x - 1) {
+      State* st = m.st;
+      st->blocks_touched += (unsigned long long)nt;
+      st->frames += 1;
+      st->sticky_err |= fe;
+      *m.frame_err = 0;
+      *m.n_touched = 0;
+      st->ticket = 0;
+    }
+  }
+  __syncthreads();
+  const int nt = head[0];
+  const bool skip = head[1] != 0;
   const int tid = threadIdx.x;
   unsigned long long merged = 0;
   const int g = (int)gridDim.x;
@@ -62,18 +88,6 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
     unsigned long long t = 0;
     for (int w = 0; w < kMergeThreads / 32; ++w) t += red[w];
     if (t) atomicAdd(&m.st->voxels_merged, t);
-    __threadfence();
-    const unsigned ticket = atomicAdd(&m.st->ticket, 1u);
-    if (ticket == gridDim.x - 1) {  // last CTA: every CTA has finished reading
-      __threadfence();
-      State* st = m.st;
-      st->blocks_touched += (unsigned long long)nt;
-      st->frames += 1;
-      st->sticky_err |= *m.frame_err;
-      *m.frame_err = 0;
-      *m.n_touched = 0;
-      st->ticket = 0;
-    }
   }
 }
 
@@ -88,7 +102,170 @@ __global__ void zero_pool_kernel(SubmapDev m, int bytes_per_block) {
   }
 }
 
+// The per-scan set `which` of a pipelined submap: a describes set 0 (and
+// everything the sets share), b the second set (a copy of a but for acc,
+// touch, touched, n_touched and frame_err).
+__device__ __forceinline__ SubmapDev pick_set(const SubmapDev& a, const SubmapDev& b, int which) {
+  SubmapDev m = a;
+  if (which) {
+    m.acc = b.acc;
+    m.touch = b.touch;
+    m.touched = b.touched;
+    m.n_touched = b.n_touched;
+    m.frame_err = b.frame_err;
+  }
+  return m;
+}
+
+// Merge the first nt touched blocks of set m: items first, first + step, ...
+// of four consecutive blocks per 256-thread CTA (a pair per half CTA, loads of
+// both in flight).  Returns the voxels this thread merged.
+__device__ __noinline__ int merge_set(const SubmapDev& m, int nt, bool skip, int first, int step, int tid) {
+  const int half = tid / kMergeThreads, sub = tid % kMergeThreads;
+  int merged = 0;
+  for (int item = first;; item += step) {
+    const int j = 4 * item + 2 * half;
+    if (j >= nt) break;
+    const int j1 = j + 1 < nt ? j + 1 : -1;
+    merged += m.storage == CVX_STORE_F32 ? merge_two<0>(m, j, j1, skip, sub) : merge_two<1>(m, j, j1, skip, sub);
+  }
+  return merged;
+}
+
+// Sum of one value over a 256-thread CTA (thread 0 gets it).
+__device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kTileThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+// Per-scan words of a pipelined submap as one launch sees them.  Thread 0 of
+// every CTA reads them on entry and then takes a ticket (a fence orders the
+// reads first; nothing of the CTA is in flight yet, so it costs little).  The
+// CTA drawing the last ticket knows that every CTA has read, and at once
+// closes the pending scan's frame (counters, sticky error, its set cleared
+// for reuse; the merging CTAs work from the values they read), sets pending
+// to `pend_after` and flips the parity when asked.  No CTA waits at its end.
+struct PipeHead {
+  int par;       // set this launch accumulates into
+  int pending;   // set par ^ 1 holds a scan to merge
+  int nt;        // its touched blocks
+  int fe;        // its error bits
+};
+
+__device__ __forceinline__ void pipe_head(const SubmapDev& a, const SubmapDev& b, int pend_after, bool flip,
+                                          PipeHead* h) {
+  if (threadIdx.x == 0) {
+    State* st = a.st;
+    const int par = *((volatile int32_t*)&st->parity);
+    const int pend = *((volatile int32_t*)&st->pending);
+    int32_t* ntp = par ? a.n_touched : b.n_touched;   // the pending set is par ^ 1
+    int32_t* fep = par ? a.frame_err : b.frame_err;
+    const int nt = pend ? min(*((volatile int32_t*)ntp), a.max_blocks) : 0;
+    const int fe = pend ? *((volatile int32_t*)fep) : 0;
+    h->par = par;
+    h->pending = pend;
+    h->nt = nt;
+    h->fe = fe;
+    __threadfence();
+    if (atomicAdd(&st->ticket, 1u) == gridDim.x - 1) {
+      if (pend) {
+        st->blocks_touched += (unsigned long long)nt;
+        st->frames += 1;
+        st->sticky_err |= fe;
+        *fep = 0;
+        *ntp = 0;
+      }
+      st->pending = pend_after;
+      if (flip) st->parity = par ^ 1;
+      st->ticket = 0;
+    }
+  }
+  __syncthreads();
+}
+
+// Pipelined per-scan kernel.  The first sc.n_tiles CTAs integrate this
+// scan's tiles into set parity; the n_merge CTAs after them merge the scan
+// the previous call integrated (set parity ^ 1, if one is pending), filling
+// the SMs the last tiles leave idle.  The tiles read neither D nor
+// W, and the two sets share only the block hash and pool, so results equal
+// merging each scan before the next one starts.  The per-scan words do not
+// change during the launch: pipe_close_kernel, launched after it, closes the
+// merged frame, makes this scan the pending one and flips the parity.
+template <int kVariant>
+__global__ void __launch_bounds__(kTileThreads, 5) integrate_pipelined_kernel(SubmapDev a, SubmapDev b, ScanDev sc,
+                                                                           int lb, int n_merge) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ unsigned long long red[kTileThreads / 32];
+  const int par = *((volatile int32_t*)&a.st->parity);
+  if ((int)blockIdx.x < sc.n_tiles) {
+    integrate_tile_v<kVariant>(pick_set(a, b, par), sc, (int)blockIdx.x, smem, lb);
+    return;
+  }
+  if (*((volatile int32_t*)&a.st->pending) == 0) return;   // uniform over the merging CTAs
+  const SubmapDev prev = pick_set(a, b, par ^ 1);
+  const int nt = min(*((volatile int32_t*)prev.n_touched), prev.max_blocks);
+  const bool skip = *((volatile int32_t*)prev.frame_err) != 0;
+  const int merged = merge_set(prev, nt, skip, (int)blockIdx.x - sc.n_tiles, n_merge, threadIdx.x);
+  const unsigned long long t = cta_sum((unsigned long long)merged, red);
+  if (threadIdx.x == 0 && t) atomicAdd(&a.st->voxels_merged, t);
+}
+
+// One thread, after integrate_pipelined_kernel: close the frame it merged
+// (counters, sticky error, its set cleared for reuse), make the scan it
+// accumulated the pending one and flip the parity.
+__global__ void pipe_close_kernel(SubmapDev a, SubmapDev b) {
+  State* st = a.st;
+  const int par = st->parity;
+  if (st->pending) {
+    int32_t* ntp = par ? a.n_touched : b.n_touched;   // the pending set is par ^ 1
+    int32_t* fep = par ? a.frame_err : b.frame_err;
+    st->blocks_touched += (unsigned long long)min(*ntp, a.max_blocks);
+    st->frames += 1;
+    st->sticky_err |= *fep;
+    *fep = 0;
+    *ntp = 0;
+  }
+  st->pending = 1;
+  st->parity = par ^ 1;
+}
+
+using PipelinedFn = void (*)(SubmapDev, SubmapDev, ScanDev, int, int);
+const PipelinedFn kPipelined[6] = {integrate_pipelined_kernel<0>, integrate_pipelined_kernel<1>,
+                                   integrate_pipelined_kernel<2>, integrate_pipelined_kernel<3>,
+                                   integrate_pipelined_kernel<4>, integrate_pipelined_kernel<5>};
+
+// Merge the pending scan of a pipelined submap (no-op when none is pending).
+// discard: clear its sums without touching D and W.
+__global__ void __launch_bounds__(kTileThreads) flush_kernel(SubmapDev a, SubmapDev b, int discard) {
+  __shared__ PipeHead h;
+  __shared__ unsigned long long red[kTileThreads / 32];
+  pipe_head(a, b, 0, false, &h);
+  if (!h.pending) return;   // uniform over the grid
+  const int merged =
+      merge_set(pick_set(a, b, h.par ^ 1), h.nt, discard || h.fe != 0, blockIdx.x, gridDim.x, threadIdx.x);
+  const unsigned long long t = cta_sum((unsigned long long)merged, red);
+  if (threadIdx.x == 0 && t) atomicAdd(&a.st->voxels_merged, t);
+}
+
 }  // namespace
+
+namespace covox {
+
+cvx_status flush_pending(cvx_submap* map, cudaStream_t s, bool discard) {
+  if (!map->pipelined || !map->maybe_pending) return CVX_OK;
+  COVOX_LAUNCH(kKFlush, s, flush_kernel<<<num_sms(), kTileThreads, 0, s>>>(map->dev, map->dev_b, discard ? 1 : 0));
+  if (cudaGetLastError() != cudaSuccess) return CVX_ERR_CUDA;
+  map->maybe_pending = false;
+  return CVX_OK;
+}
+
+}  // namespace covox
 
 // ===================================================================== C ABI
 namespace {
@@ -232,6 +409,23 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
                            (int)tile_smem_bytes(kMaxLocalBlocks));
     attr_set = true;
   }
+  if (map->pipelined) {
+    static bool pattr_set = false;
+    if (!pattr_set) {
+      for (int v = 0; v < 6; ++v)
+        cudaFuncSetAttribute((const void*)kPipelined[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem_bytes(kMaxLocalBlocks));
+      pattr_set = true;
+    }
+    const int n_merge = num_sms();
+    const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff)];
+    COVOX_LAUNCH(kKPipelined, s,
+                 pf<<<n_merge + sc.n_tiles, kTileThreads, smem, s>>>(map->dev, map->dev_b, sc, lb, n_merge));
+    COVOX_LAUNCH(kKPipeClose, s, pipe_close_kernel<<<1, 1, 0, s>>>(map->dev, map->dev_b));
+    if (cudaGetLastError() != cudaSuccess) return CVX_ERR_CUDA;
+    map->maybe_pending = true;
+    return CVX_OK;
+  }
   const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff)];
   COVOX_LAUNCH(kKAccum, s, fn<<<sc.n_tiles, kTileThreads, smem, s>>>(map->dev, sc, lb));
   const int grid = std::min<int>(map->dev.max_blocks, num_sms() * 2);
@@ -247,6 +441,7 @@ cvx_status cvx_extract_blocks(cvx_submap* map, int64_t capacity, int32_t* keys, 
   if (!map || !n_out || capacity < 0) return CVX_ERR_INVALID_ARG;
   if (keys && capacity > 0 && (!dist || !weight)) return CVX_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (flush_pending(map, s, false) != CVX_OK) return CVX_ERR_CUDA;
   int32_t nb = 0;
   if (cudaMemcpyAsync(&nb, &map->dev.st->n_blocks, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
@@ -277,6 +472,7 @@ cvx_status cvx_reset_submap(cvx_submap* map, void* stream) {
   if (!map) return CVX_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   map->last_stream = s;
+  if (flush_pending(map, s, true) != CVX_OK) return CVX_ERR_CUDA;
   const int bpb = (int)(kVoxPerBlock * map->bytes_per_vox);
   COVOX_LAUNCH(kKZeroPool, s, zero_pool_kernel<<<num_sms() * 4, 256, 0, s>>>(map->dev, bpb));
   cudaMemsetAsync(map->dev.keys, 0xff, (size_t)map->p.hash_slots * 8, s);
@@ -287,6 +483,7 @@ cvx_status cvx_reset_submap(cvx_submap* map, void* stream) {
 
 cvx_status cvx_submap_counters(cvx_submap* map, cvx_counters* out) {
   if (!map || !out) return CVX_ERR_INVALID_ARG;
+  if (flush_pending(map, map->last_stream, false) != CVX_OK) return CVX_ERR_CUDA;
   State st;
   if (cudaMemcpyAsync(&st, map->dev.st, sizeof(State), cudaMemcpyDeviceToHost, map->last_stream) !=
           cudaSuccess ||
@@ -313,6 +510,13 @@ cvx_status cvx_submap_status(cvx_submap* map) {
     return CVX_ERR_CUDA;
   }
   return status_from_bits(st.sticky_err | st.frame_err | st.frame_err_b);
+}
+
+cvx_status cvx_flush_submap(cvx_submap* map, void* stream) {
+  if (!map) return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  map->last_stream = s;
+  return flush_pending(map, s, false);
 }
 
 void cvx_destroy(cvx_submap* map) {

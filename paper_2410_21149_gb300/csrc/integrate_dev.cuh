@@ -210,9 +210,11 @@ __device__ __forceinline__ void fixed_add(unsigned* lo, int* hi, int S, long lon
   atomicAdd(hi, (int)(X >> S));
 }
 
+// X * 2^-F rounded once to FP32: the integer conversion rounds, the scaling
+// by a power of two is exact (no FP64 anywhere on the GPU path).
 __device__ __forceinline__ float fixed_value(unsigned lo, int hi, int S, float inv_scale) {
   const long long X = ((long long)hi << S) + (long long)lo;
-  return (float)((double)X * (double)inv_scale);
+  return __ll2float_rn(X) * inv_scale;
 }
 
 // Pool index of a block through the CTA's block -> pool cache.  The first
@@ -332,6 +334,15 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     unsigned long long key = pack_key(d.v[0] >> 3, d.v[1] >> 3, d.v[2] >> 3);
     int slot = kLocal ? local_slot(t, lb, key) : -1;
     int gpool = slot < 0 ? cached_pool(m, t, key) : -1;
+    // The band ends in the block of its last cell; most bands meet one or two
+    // blocks, so the end block is looked up here, with every lane of the warp,
+    // and only a block met in between is looked up inside the loop.
+    const unsigned long long key_end = pack_key(d.e[0] >> 3, d.e[1] >> 3, d.e[2] >> 3);
+    int slot_end = slot, gpool_end = gpool;
+    if (key_end != key) {
+      slot_end = kLocal ? local_slot(t, lb, key_end) : -1;
+      gpool_end = slot_end < 0 ? cached_pool(m, t, key_end) : -1;
+    }
     for (;;) {
       const float dc = fminf(fmaxf(dist, -m.trunc), m.trunc);
       float w = w0;
@@ -367,8 +378,13 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
       l = (l & ~mask) | f;
       if (f == (sk > 0 ? 0 : mask)) {   // crossed into the neighbouring block
         key += sk > 0 ? (1ull << shift) : (0ull - (1ull << shift));
-        slot = kLocal ? local_slot(t, lb, key) : -1;
-        gpool = slot < 0 ? cached_pool(m, t, key) : -1;
+        if (key == key_end) {
+          slot = slot_end;
+          gpool = gpool_end;
+        } else {
+          slot = kLocal ? local_slot(t, lb, key) : -1;
+          gpool = slot < 0 ? cached_pool(m, t, key) : -1;
+        }
       }
     }
   }

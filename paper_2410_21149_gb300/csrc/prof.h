@@ -18,7 +18,10 @@ enum KernelKind : int {
   kKMlpBwd = 7,     // weight model backward + reduction
   kKAdam = 8,       // weight model optimiser step
   kKTargets = 9,    // training targets
-  kNumKinds = 10
+  kKPipelined = 10, // pipelined per-scan kernel (tiles + merges of the previous scan)
+  kKFlush = 11,     // merge of a pipelined submap's pending scan
+  kKPipeClose = 12, // pipelined per-scan bookkeeping after each scan
+  kNumKinds = 13
 };
 
 void prof_begin(int kind, cudaStream_t s);

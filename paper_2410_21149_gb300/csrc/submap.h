@@ -16,6 +16,7 @@ struct cvx_submap {
   covox::SubmapDev dev;
   covox::SubmapDev dev_b;   // the second per-scan set of a pipelined submap
   bool pipelined;
+  bool maybe_pending;       // a pipelined per-scan launch may have left a scan unmerged
   size_t bytes_per_vox;
   cudaStream_t last_stream;
   struct Alloc {
@@ -37,6 +38,10 @@ inline int num_sms() {
   }
   return n;
 }
+
+// Merge the scan a pipelined submap's last per-scan launch left pending
+// (discard: drop its sums instead).  No-op for other submaps.
+cvx_status flush_pending(cvx_submap* map, cudaStream_t s, bool discard);
 
 constexpr int kDefaultLocalBlocks = 8;
 constexpr int kMaxLocalBlocks = 16;   // 8 KB of fixed-point sums each

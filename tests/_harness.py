@@ -15,7 +15,7 @@ def int_params(wl: sg.Workload, scan: sg.Scan, **over):
     return cvx.integrate_params(**kw)
 
 
-def run_gpu(wl: sg.Workload, storage=None, max_blocks=1 << 17, point_weights=None, **over):
+def run_gpu(wl: sg.Workload, storage=None, max_blocks=1 << 17, point_weights=None, pipelined=False, **over):
     """Integrate every submap of the workload; returns a list of
     (keys [nb,3] int32, D [nb,512] float64 metres, W [nb,512] float64, counters)."""
     import torch
@@ -23,7 +23,8 @@ def run_gpu(wl: sg.Workload, storage=None, max_blocks=1 << 17, point_weights=Non
     storage = wl.storage if storage is None else storage
     out = []
     for m, sm in enumerate(wl.submaps):
-        sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks)
+        sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
+                         pipelined=pipelined)
         for k, sc in enumerate(sm.scans):
             pts = torch.from_numpy(np.ascontiguousarray(sc.points)).cuda()
             pw = None
