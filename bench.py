@@ -216,11 +216,19 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
     subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
                        pipelined=pipelined) for sm in wl.submaps]
     handles = [s.handle for s in subs]
-    items = []
-    for m, sm in enumerate(wl.submaps):
-        for sc in sm.scans:
-            items.append((m, torch.from_numpy(np.ascontiguousarray(sc.points)).cuda(), sc.T_sub_sensor, sc))
-    n_points = sum(int(p.shape[0]) for _, p, _, _ in items)
+    # every scan's points in one device buffer (views per scan) with a pinned
+    # host copy for the end-to-end timing
+    scans_all = [(m, sc) for m, sm in enumerate(wl.submaps) for sc in sm.scans]
+    n_points = sum(int(sc.points.shape[0]) for _, sc in scans_all)
+    host_all = torch.empty((n_points, 3), dtype=torch.float32).pin_memory()
+    dev_all = torch.empty((n_points, 3), dtype=torch.float32, device="cuda")
+    items, o = [], 0
+    for m, sc in scans_all:
+        n = int(sc.points.shape[0])
+        host_all[o:o + n] = torch.from_numpy(np.ascontiguousarray(sc.points))
+        items.append((m, dev_all[o:o + n], sc.T_sub_sensor, sc))
+        o += n
+    dev_all.copy_(host_all)
 
     def prm(sc, ppc=0, lb=0):
         return cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range, sc.sensor,
@@ -244,6 +252,8 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
         reset(stream)
         for m, p, T, sc in items:
             subs[m].integrate(p, T, prm(sc, ppc, lb), None, stream)
+        for s in subs:
+            s.flush(stream)      # pipelined submaps: each one's last scan
 
     def graph_time(step):
         for _ in range(2):
@@ -269,8 +279,10 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
     # one eager step: counters, kernel time, per-wave phase times, status
     _capi.cvx_profile_start(1 << 20)
     _capi.cvx_batch_timing(batch, True)
+    l0 = _capi.cvx_launch_count()
     step_batched()
     torch.cuda.synchronize()
+    launches = _capi.cvx_launch_count() - l0
     _capi.cvx_profile_stop()
     _capi.cvx_batch_timing(batch, False)
     prof = _capi.cvx_profile_read()
@@ -280,6 +292,23 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
     tot = {k: sum(c[k] for c in cnt) for k in cnt[0]}
     rmse = multi_rmse(wl, subs, storage)
     ms_s = graph_time(step_seq) if sequential else None
+
+    # end to end through the public API: pinned host points copied in, one
+    # batched launch, every submap's counters read back
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            dev_all.copy_(host_all, non_blocking=True)
+        step_batched()
+        return [s.counters() for s in subs]
+
+    for _ in range(warmup):
+        e2e_step()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    barrier(ws)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws) / steps
     kern_ms = prof["batched_kernel"][0] / max(prof["batched_kernel"][1], 1)
     S = 8 if storage == 0 else 4
     kbytes = 12 * n_points + 2 * S * tot["voxels_merged"] + 16 * tot["blocks_touched"]
@@ -290,8 +319,11 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
             "input_points": n_points, "observations": tot["observations"], "voxels_merged": tot["voxels_merged"],
             "blocks_touched": tot["blocks_touched"], "blocks_allocated": tot["n_blocks"],
             "scans": len(items), "submaps": len(subs), "tuned": {"pts_per_cta": ppc, "local_blocks": lb},
+            "launches_per_step": launches,
             "batched_kernel_ms": kern_ms, "kernel_bytes": kbytes, "sdf_rmse_m": rmse,
             "reset_and_other_ms": ms_b - kern_ms, "pipelined": pipelined,
+            "e2e_ms_per_step": e2e_ms, "h2d_bytes_per_step": int(n_points * 12),
+            "d2h_bytes_per_step": 48 * len(subs),
             "phases": {"waves": int(len(phases)), "tiles_ms": float(phases[:, 0].sum()),
                        "merge_ms": float(phases[:, 1].sum()), "bookkeeping_ms": float(phases[:, 2].sum()),
                        "per_wave_median_ms": [float(x) for x in np.median(phases, 0)]}}
@@ -322,12 +354,15 @@ def run_ours(args):
         return cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range, sc0.sensor,
                                     sc0.height, sc0.width, ppc, lb)
 
+    pipelined = args.pipelined == 1
     if args.ppc == 0:   # launch shape from the autotuner (first 20 frames, cached per device)
         from paper_2410_21149_gb300 import autotune
-        tuned = autotune.tune_scans(sm.voxel_size, sm.trunc, wl.max_weight, 0,
-                                    [(pts[f], Ts[f]) for f in range(min(20, len(Ts)))], prm_of,
-                                    max_blocks=args.max_blocks)
-        args.ppc, args.lb = tuned["pts_per_cta"], tuned["local_blocks"]
+        sample = [(pts[f], Ts[f]) for f in range(min(20, len(Ts)))]
+        tuned = {p: autotune.tune_scans(sm.voxel_size, sm.trunc, wl.max_weight, 0, sample, prm_of,
+                                        max_blocks=args.max_blocks, pipelined=p)
+                 for p in ((False, True) if args.pipelined < 0 else (pipelined,))}
+        pipelined = min(tuned, key=lambda p: tuned[p]["ms"])
+        args.ppc, args.lb = tuned[pipelined]["pts_per_cta"], tuned[pipelined]["local_blocks"]
     params = prm_of(args.ppc, args.lb)
     stream = torch.cuda.Stream()
     max_blocks = args.max_blocks
@@ -335,13 +370,14 @@ def run_ours(args):
     def make_sub(storage):
         with torch.cuda.stream(stream):
             s = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
-                           stream=stream)
+                           stream=stream, pipelined=pipelined)
         return s
 
     def step(sub):
         sub.reset(stream)
         for f in range(F):
             sub.integrate(pts[f], Ts[f], params, None, stream)
+        sub.flush(stream)     # pipelined submap: the last frame's merge (no-op otherwise)
 
     def capture(sub):
         for _ in range(2):      # warm up the allocator and the kernels outside capture
@@ -382,9 +418,6 @@ def run_ours(args):
     ms32 = timed(g32, args.steps, args.warmup)
     clk = clocks.stop()
     ms32 = max_over_ranks(ms32, ws)
-    # kernel launches inside the timed region: graph replays launch the
-    # captured kernels; count them from one captured step
-    per_step_launches = 1 + 3 * F
 
     # per-kernel durations: profiled eager pass over the same steps (the
     # library counts every launch it issues: one step's count checks the
@@ -462,6 +495,7 @@ def run_ours(args):
     bytes_kernel = {
         "integrate_kernel": (12 * F * N + 16 * blocks + 12 * new_blocks) / F,
         "merge_kernel": 2 * S32 * merged / F,
+        "integrate_pipelined_kernel": (12 * F * N + 16 * blocks + 12 * new_blocks + 2 * S32 * merged) / F,
     }
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
@@ -487,7 +521,7 @@ def run_ours(args):
         "config": {"workload": wl.name, "frames_per_step": F, "points_per_frame": N,
                    "voxel_size_m": sm.voxel_size, "trunc_m": sm.trunc, "weight": "quadratic+linear-dropoff",
                    "storage": "f32", "step": "clear submap + integrate all frames (CUDA graph replay)",
-                   "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb},
+                   "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb, "pipelined": pipelined},
                    "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (F * N * 12 / 1e6),
                    "parallelism": f"replica x{ws} (one submap sequence per GPU)"},
         "voxel_updates_per_s": tot_obs / sec32,
@@ -506,8 +540,10 @@ def run_ours(args):
         "kernel_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items() if v[1]},
         "e2e": {"value": tot_valid / (e2e_ms / 1e3 / args.steps), "unit": "points/s",
                 "h2d_bytes_per_step": int(F * N * 12), "d2h_bytes_per_step": 48},
-        "gpu_launches": per_step_launches * args.steps,
-        "gpu_launches_per_step_counted": launches_per_step,
+        # graph replays launch the kernels one captured step launched; the
+        # library counts every launch it issues (eager step above)
+        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches_per_step": launches_per_step,
         "clocks": clk,
     }
     if not args.no_learned:
@@ -647,8 +683,13 @@ def run_lidar(args, ws, rank, peaks, peak_src):
         "counts_per_step": {k: r[k] for k in ("points", "observations", "voxels_merged", "blocks_touched",
                                               "blocks_allocated")},
         "autotuned": r["tuned"], "batched_phases": r["phases"],
-        "gpu_launches": (1 + r["submaps"]) * args.steps, "clocks": clk,
+        "e2e": {"value": pts / (r["e2e_ms_per_step"] / 1e3), "unit": "points/s",
+                "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"]},
+        "gpu_launches": r["launches_per_step"] * args.steps, "gpu_launches_per_step": r["launches_per_step"],
+        "clocks": clk,
     }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(sg.make_c3(n_scans=50), args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -716,6 +757,8 @@ def main():
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--ppc", type=int, default=0, help="points per CTA tile (0: autotuned)")
     ap.add_argument("--lb", type=int, default=0, help="shared block slots per CTA (-1: global atomics)")
+    ap.add_argument("--pipelined", type=int, default=-1, choices=[-1, 0, 1],
+                    help="pipelined submaps on the per-scan path (-1: autotuned with the launch shape)")
     ap.add_argument("--max-blocks", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -100,14 +100,17 @@ def tune(key: str, make_run, candidates: Iterable[Tuple[int, int]] = DEFAULT_CAN
 
 def tune_scans(voxel_size: float, trunc: float, max_weight: float, storage: int, scans: Sequence[tuple],
                params_fn, max_blocks: int = 1 << 16, force: bool = False,
-               candidates: Iterable[Tuple[int, int]] = DEFAULT_CANDIDATES) -> Dict[str, float]:
+               candidates: Iterable[Tuple[int, int]] = DEFAULT_CANDIDATES,
+               pipelined: bool = False) -> Dict[str, float]:
     """Per-scan path on a scratch submap.  scans: [(points tensor, T)];
-    params_fn(ppc, lb) -> cvx_integrate_params."""
+    params_fn(ppc, lb) -> cvx_integrate_params.  pipelined: time a pipelined
+    submap (each scan's merge overlapped with the next scan; flushed at the
+    end), cached under its own key."""
     from . import Submap
     p0 = params_fn(0, 0)
     key = signature("scan", p0.sensor, p0.height, p0.width, voxel_size, trunc, p0.weight_mode,
-                    p0.dropoff, storage)
-    sub = Submap(voxel_size, trunc, max_weight, storage, max_blocks=max_blocks)
+                    p0.dropoff, storage) + ("|p1" if pipelined else "")
+    sub = Submap(voxel_size, trunc, max_weight, storage, max_blocks=max_blocks, pipelined=pipelined)
 
     def make_run(ppc, lb):
         prm = params_fn(ppc, lb)
@@ -116,6 +119,7 @@ def tune_scans(voxel_size: float, trunc: float, max_weight: float, storage: int,
             sub.reset()
             for pts, T in scans:
                 sub.integrate(pts, T, prm)
+            sub.flush()
         return run
 
     try:

@@ -163,7 +163,16 @@ __device__ void wave_bookkeeping(const BatchDev& b, int w, const int* nt_prefix)
     st->sticky_err |= *m.frame_err;
     *m.frame_err = 0;
     *m.n_touched = 0;
+    if (!b.pipelined) st->epoch += 1;   // the submap's next scan takes the next epoch
   }
+}
+
+// pipelined: the tiles of wave w are done, so their submaps' next scans take
+// the next epoch (CTA 0, after the step's barrier)
+__device__ void wave_epoch(const BatchDev& b, int w) {
+  if (blockIdx.x != 0) return;
+  for (int s = b.wave_begin[w] + threadIdx.x; s < b.wave_begin[w + 1]; s += blockDim.x)
+    view(b, b.scan_map[s], w).st->epoch += 1;
 }
 
 template <int kVariant>
@@ -224,6 +233,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
     if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 1);
     if (w > 0) wave_bookkeeping(b, w - 1, nt_prefix);
+    if (w < b.n_waves) wave_epoch(b, w);
     if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 2);
     stamp(b, 3 * w + 3);

@@ -26,7 +26,7 @@ struct State {
   int32_t frame_err_b;
   int32_t parity;       // pipelined per-scan path: set the next scan accumulates into
   int32_t pending;      // pipelined per-scan path: set parity ^ 1 holds an unmerged scan
-  int32_t pad;
+  uint32_t epoch;       // scans whose tiles have completed; the running scan's epoch is epoch + 1
   unsigned long long frames, valid_pts, obs, voxels_merged, blocks_touched;
 };
 
@@ -34,7 +34,9 @@ struct State {
 struct SubmapDev {
   unsigned long long* keys;   // [slots] packed block keys, kEmptyKey when free
   int32_t* vals;              // [slots] pool index of the slot's block (-1: not yet published, -3: none)
-  int32_t* touch;             // [max_blocks] per-scan touched-list position, -1 when untouched
+  uint32_t* epochs;           // [slots] epoch of the last scan that touched the slot's block, or
+                              // nullptr: per-scan touch map below instead
+  int32_t* touch;             // [max_blocks] per-scan touched mark (-1 when untouched), or nullptr
   int32_t* block_keys;        // [max_blocks,3] integer block coordinates
   void* D;                    // [max_blocks,512] float or half (D / trunc)
   void* W;                    // [max_blocks,512] float or half
@@ -78,29 +80,6 @@ __device__ __forceinline__ uint32_t hash_key(unsigned long long k) {
   k *= 0xc4ceb9fe1a85ec53ull;
   k ^= k >> 33;
   return (uint32_t)k;
-}
-
-// Insert-or-find ("activate", Sec. III-B): returns the slot of `key`, or -1
-// if the bounded probe found no room.  *inserted tells whether this call
-// claimed the slot.
-__device__ __forceinline__ int hash_activate(const SubmapDev& m, unsigned long long key,
-                                             bool* inserted) {
-  uint32_t s = hash_key(key) & m.slot_mask;
-  *inserted = false;
-  for (int p = 0; p < m.max_probe; ++p) {
-    unsigned long long cur = *((volatile unsigned long long*)(m.keys + s));
-    if (cur == key) return (int)s;
-    if (cur == kEmptyKey) {
-      unsigned long long old = atomicCAS(m.keys + s, kEmptyKey, key);
-      if (old == kEmptyKey) {
-        *inserted = true;
-        return (int)s;
-      }
-      if (old == key) return (int)s;
-    }
-    s = (s + 1) & m.slot_mask;
-  }
-  return -1;
 }
 
 // Lookup only (keys are not modified by the caller's kernel).

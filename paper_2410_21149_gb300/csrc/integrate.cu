@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
       st->blocks_touched += (unsigned long long)nt;
       st->frames += 1;
       st->sticky_err |= fe;
+      st->epoch += 1;   // the next scan's tiles take the next epoch
       *m.frame_err = 0;
       *m.n_touched = 0;
       st->ticket = 0;
@@ -233,6 +234,7 @@ __global__ void pipe_close_kernel(SubmapDev a, SubmapDev b) {
   }
   st->pending = 1;
   st->parity = par ^ 1;
+  st->epoch += 1;   // the next scan's tiles take the next epoch
 }
 
 using PipelinedFn = void (*)(SubmapDev, SubmapDev, ScanDev, int, int);
@@ -325,7 +327,8 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   SubmapDev& d = m->dev;
   d.keys = (unsigned long long*)sub_alloc(m, slots * 8);
   d.vals = (int32_t*)sub_alloc(m, slots * 4);
-  d.touch = (int32_t*)sub_alloc(m, nb * 4);
+  d.epochs = (uint32_t*)sub_alloc(m, slots * 4);
+  d.touch = nullptr;   // scan epochs in the slots mark touched blocks
   d.block_keys = (int32_t*)sub_alloc(m, nb * 12);
   d.D = sub_alloc(m, nb * kVoxPerBlock * m->bytes_per_vox);
   d.W = sub_alloc(m, nb * kVoxPerBlock * m->bytes_per_vox);
@@ -337,9 +340,8 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   SubmapDev& db = m->dev_b;
   if (m->pipelined) {   // second per-scan set: sums, touch map, touched list
     db.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
-    db.touch = (int32_t*)sub_alloc(m, nb * 4);
     db.touched = (int32_t*)sub_alloc(m, nb * 4);
-    expect = 12;
+    expect = 11;
   }
   if (m->n_allocs != expect) {
     sub_free_all(m);
@@ -359,11 +361,9 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.max_w = p->max_weight;
   if (m->pipelined) {
     float2* acc_b = db.acc;
-    int32_t* touch_b = db.touch;
     int32_t* touched_b = db.touched;
     db = d;
     db.acc = acc_b;
-    db.touch = touch_b;
     db.touched = touched_b;
     db.n_touched = &d.st->n_touched_b;
     db.frame_err = &d.st->frame_err_b;
@@ -372,14 +372,13 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   m->last_stream = s;
   cudaMemsetAsync(d.keys, 0xff, slots * 8, s);
   cudaMemsetAsync(d.vals, 0xff, slots * 4, s);
-  cudaMemsetAsync(d.touch, 0xff, nb * 4, s);
+  cudaMemsetAsync(d.epochs, 0, slots * 4, s);
   cudaMemsetAsync(d.D, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.W, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
   cudaMemsetAsync(d.st, 0, sizeof(State), s);
   if (m->pipelined) {
     cudaMemsetAsync(db.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
-    cudaMemsetAsync(db.touch, 0xff, nb * 4, s);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();

@@ -20,45 +20,82 @@ constexpr int kTileBlocks = 64;      // distinct blocks recorded per tile (power
 constexpr int kMapDead = -3;         // vals[] marker: block unusable (pool exhausted)
 constexpr long long kSpinLimit = 1 << 22;
 
-// Global activation of one block (insert-or-find, pool allocation, entry in
-// the scan's touched list).  Returns the pool index or -1 (error recorded).
-__device__ inline int global_activate(const SubmapDev& m, unsigned long long key) {
-  bool inserted;
-  const int s = hash_activate(m, key, &inserted);
-  if (s < 0) {
-    atomicOr(m.frame_err, kErrCapacity);
-    return -1;
-  }
-  int pool;
-  if (inserted) {
-    pool = atomicAdd(&m.st->n_blocks, 1);
-    if (pool >= m.max_blocks) {
-      atomicOr(m.frame_err, kErrCapacity);
-      atomicExch(m.vals + s, kMapDead);
-      return -1;
+// The scan's entry in its touched list (one per block and scan).
+__device__ __forceinline__ void append_touched(const SubmapDev& m, int pool) {
+  const int j = atomicAdd(m.n_touched, 1);   // j < max_blocks: each block once per scan
+  m.touched[j] = pool;
+}
+
+// First activation of a block in this scan: touch map variant (no epochs).
+__device__ __forceinline__ void touch_block(const SubmapDev& m, int pool) {
+  if (*((volatile int32_t*)(m.touch + pool)) == -1 && atomicCAS(m.touch + pool, -1, -2) == -1)
+    append_touched(m, pool);
+}
+
+// Global activation of one block ("activate", Sec. III-B: insert-or-find,
+// pool index by atomic bump for a new block, entry in the scan's touched
+// list).  Returns the pool index or -1 (error recorded).
+//
+// A slot holds the packed key, the pool index and (when m.epochs is set) the
+// epoch of the last scan that touched the block.  The probe loads all three
+// of a slot at once -- their addresses do not depend on each other -- so a
+// block that this scan has already activated costs one round trip.  The
+// first toucher of a scan is the thread whose CAS moves the slot's epoch to
+// `ep`; the inserter of a new block sets the epoch before it publishes the
+// pool index, so a thread that read a stale epoch fails its CAS.
+__device__ inline int global_activate(const SubmapDev& m, unsigned long long key, uint32_t ep) {
+  uint32_t s = hash_key(key) & m.slot_mask;
+  for (int p = 0; p < m.max_probe; ++p) {
+    const unsigned long long cur = *((volatile unsigned long long*)(m.keys + s));
+    int pool = *((volatile int32_t*)(m.vals + s));
+    uint32_t e = m.epochs ? *((volatile uint32_t*)(m.epochs + s)) : 0u;
+    bool found = cur == key;
+    if (cur == kEmptyKey) {
+      const unsigned long long old = atomicCAS(m.keys + s, kEmptyKey, key);
+      if (old == kEmptyKey) {   // inserted: allocate, publish, first toucher
+        pool = atomicAdd(&m.st->n_blocks, 1);
+        if (pool >= m.max_blocks) {
+          atomicOr(m.frame_err, kErrCapacity);
+          atomicExch(m.vals + s, kMapDead);
+          return -1;
+        }
+        m.block_keys[3 * pool] = (int)((key >> 42) & 0x1fffff) - (1 << 20);
+        m.block_keys[3 * pool + 1] = (int)((key >> 21) & 0x1fffff) - (1 << 20);
+        m.block_keys[3 * pool + 2] = (int)(key & 0x1fffff) - (1 << 20);
+        if (m.epochs) {
+          m.epochs[s] = ep;
+          __threadfence();
+        }
+        atomicExch(m.vals + s, pool);   // publish
+        if (m.epochs) append_touched(m, pool);
+        else touch_block(m, pool);
+        return pool;
+      }
+      found = old == key;
+      pool = -1;   // read it once published
     }
-    m.block_keys[3 * pool] = (int)((key >> 42) & 0x1fffff) - (1 << 20);
-    m.block_keys[3 * pool + 1] = (int)((key >> 21) & 0x1fffff) - (1 << 20);
-    m.block_keys[3 * pool + 2] = (int)(key & 0x1fffff) - (1 << 20);
-    atomicExch(m.vals + s, pool);   // publish
-  } else {
-    pool = *((volatile int32_t*)(m.vals + s));
-    for (long long it = 0; pool == -1 && it < kSpinLimit; ++it) {   // the inserter publishes shortly
-      __nanosleep(64);
-      pool = *((volatile int32_t*)(m.vals + s));
+    if (found) {
+      for (long long it = 0; pool == -1 && it < kSpinLimit; ++it) {   // the inserter publishes shortly
+        __nanosleep(64);
+        pool = *((volatile int32_t*)(m.vals + s));
+        if (m.epochs) e = *((volatile uint32_t*)(m.epochs + s));
+      }
+      if (pool == -1) {
+        atomicOr(m.frame_err, kErrTimeout);
+        return -1;
+      }
+      if (pool < 0) return -1;   // block unusable (pool was exhausted)
+      if (m.epochs) {
+        if (e != ep && atomicCAS(m.epochs + s, e, ep) == e) append_touched(m, pool);
+      } else {
+        touch_block(m, pool);
+      }
+      return pool;
     }
-    if (pool == -1) {
-      atomicOr(m.frame_err, kErrTimeout);
-      return -1;
-    }
-    if (pool < 0) return -1;
+    s = (s + 1) & m.slot_mask;
   }
-  if (*((volatile int32_t*)(m.touch + pool)) == -1 && atomicCAS(m.touch + pool, -1, -2) == -1) {
-    const int j = atomicAdd(m.n_touched, 1);   // j < max_blocks: each block once per scan
-    m.touched[j] = pool;
-    atomicExch(m.touch + pool, j);
-  }
-  return pool;
+  atomicOr(m.frame_err, kErrCapacity);   // bounded probe found no room
+  return -1;
 }
 
 // Pool index of an already activated block (read-only probe), or -1.
@@ -221,7 +258,8 @@ __device__ __forceinline__ float fixed_value(unsigned lo, int hi, int S, float i
 // thread to meet a block activates it and publishes the index; a thread that
 // finds the entry still pending activates it itself (activation is
 // idempotent), so nobody waits.
-__device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t, unsigned long long key) {
+__device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t, unsigned long long key,
+                                           uint32_t ep) {
   const uint32_t h = slot_hash(key) >> 26;
   for (int p = 0; p < 8; ++p) {
     const int q = (h + p) & (kCache - 1);
@@ -232,16 +270,16 @@ __device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t
       own = cur == kEmptyKey;
     }
     if (own) {
-      const int pool = global_activate(m, key);
+      const int pool = global_activate(m, key, ep);
       atomicExch(t.cpool + q, pool);
       return pool;
     }
     if (cur == key) {
       const int pool = *((volatile int*)(t.cpool + q));
-      return pool != kCachePending ? pool : global_activate(m, key);
+      return pool != kCachePending ? pool : global_activate(m, key, ep);
     }
   }
-  return global_activate(m, key);
+  return global_activate(m, key, ep);
 }
 
 // Shared slot of a block in a map of lb (power of two) slots, or -1 if full.
@@ -270,6 +308,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
   }
   const TilePoints tp(sc, tile);
   const int iters = tile_iters(sc);
+  const uint32_t ep = m.epochs ? *((volatile uint32_t*)&m.st->epoch) + 1u : 0u;   // this scan's epoch
   Fixed fx;
   if (kLocal) {
     for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
@@ -333,7 +372,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     int l = local_index(d.v);
     unsigned long long key = pack_key(d.v[0] >> 3, d.v[1] >> 3, d.v[2] >> 3);
     int slot = kLocal ? local_slot(t, lb, key) : -1;
-    int gpool = slot < 0 ? cached_pool(m, t, key) : -1;
+    int gpool = slot < 0 ? cached_pool(m, t, key, ep) : -1;
     // The band ends in the block of its last cell; most bands meet one or two
     // blocks, so the end block is looked up here, with every lane of the warp,
     // and only a block met in between is looked up inside the loop.
@@ -341,7 +380,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     int slot_end = slot, gpool_end = gpool;
     if (key_end != key) {
       slot_end = kLocal ? local_slot(t, lb, key_end) : -1;
-      gpool_end = slot_end < 0 ? cached_pool(m, t, key_end) : -1;
+      gpool_end = slot_end < 0 ? cached_pool(m, t, key_end, ep) : -1;
     }
     for (;;) {
       const float dc = fminf(fmaxf(dist, -m.trunc), m.trunc);
@@ -383,7 +422,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
           gpool = gpool_end;
         } else {
           slot = kLocal ? local_slot(t, lb, key) : -1;
-          gpool = slot < 0 ? cached_pool(m, t, key) : -1;
+          gpool = slot < 0 ? cached_pool(m, t, key, ep) : -1;
         }
       }
     }
@@ -393,7 +432,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     // allocation: each distinct block of the tile's shared slots is activated once
     for (int q = tid; q < lb; q += kTileThreads) {
       const unsigned long long key = t.mkey[q];
-      t.pool[q] = key == kEmptyKey ? -1 : cached_pool(m, t, key);
+      t.pool[q] = key == kEmptyKey ? -1 : cached_pool(m, t, key, ep);
     }
     __syncthreads();
     // flush the tile's sums into the per-scan accumulators
@@ -559,7 +598,7 @@ __device__ __forceinline__ int merge_two(const SubmapDev& m, int j0, int j1, boo
     b[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     b[1] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (tid == 0) {
+  if (tid == 0 && m.touch) {
     m.touch[p0] = -1;
     if (p1 >= 0) m.touch[p1] = -1;
   }
