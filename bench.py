@@ -355,6 +355,7 @@ def run_ours(args):
                                     sc0.height, sc0.width, ppc, lb)
 
     pipelined = args.pipelined == 1
+    tune_report = None
     if args.ppc == 0:   # launch shape from the autotuner (first 20 frames, cached per device)
         from paper_2410_21149_gb300 import autotune
         sample = [(pts[f], Ts[f]) for f in range(min(20, len(Ts)))]
@@ -363,6 +364,7 @@ def run_ours(args):
                  for p in ((False, True) if args.pipelined < 0 else (pipelined,))}
         pipelined = min(tuned, key=lambda p: tuned[p]["ms"])
         args.ppc, args.lb = tuned[pipelined]["pts_per_cta"], tuned[pipelined]["local_blocks"]
+        tune_report = {("pipelined" if p else "plain"): tuned[p]["timings"] for p in tuned}
     params = prm_of(args.ppc, args.lb)
     stream = torch.cuda.Stream()
     max_blocks = args.max_blocks
@@ -521,7 +523,8 @@ def run_ours(args):
         "config": {"workload": wl.name, "frames_per_step": F, "points_per_frame": N,
                    "voxel_size_m": sm.voxel_size, "trunc_m": sm.trunc, "weight": "quadratic+linear-dropoff",
                    "storage": "f32", "step": "clear submap + integrate all frames (CUDA graph replay)",
-                   "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb, "pipelined": pipelined},
+                   "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb, "pipelined": pipelined,
+                                 "candidates_ms_20_frames": tune_report},
                    "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (F * N * 12 / 1e6),
                    "parallelism": f"replica x{ws} (one submap sequence per GPU)"},
         "voxel_updates_per_s": tot_obs / sec32,

@@ -62,18 +62,32 @@ def signature(mode: str, sensor: int, height: int, width: int, voxel_size: float
 
 
 def _time_ms(run, repeats: int) -> float:
+    """Best of `repeats` timings of run(), recorded once as a CUDA graph and
+    replayed (host launch overhead would otherwise blur candidates whose GPU
+    times are close); eager if the run cannot be captured."""
     import torch
     run()                                   # warm-up (allocations, first touch)
     torch.cuda.synchronize()
+    replay = run
+    graph = None
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            run()
+        replay = graph.replay
+    except RuntimeError:
+        graph = None
+        torch.cuda.synchronize()
     best = float("inf")
     for _ in range(repeats):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        run()
+        replay()
         e1.record()
         e1.synchronize()
         best = min(best, e0.elapsed_time(e1))
+    del graph
     return best
 
 

@@ -98,40 +98,60 @@ __device__ __forceinline__ int find_scan(const int* prefix, int lo, int hi, int 
   return lo;
 }
 
-// Merge work of wave w: every touched block of every submap of the wave, in
-// pairs per half CTA (loads of both blocks in flight).  item = pair index.
-// One item = 4 consecutive blocks (2 per half CTA); items first_item,
-// first_item + step, ... (single: only the first).
-__device__ void merge_wave(const BatchDev& b, int w, const int* nt_prefix, int first_item, int step, bool single) {
+// Merge work of wave w: every touched block of every submap of the wave,
+// taken in spans of kSpan consecutive blocks of the wave's concatenated
+// touched lists.  A span's pool indices, scans and skip flags are gathered in
+// one round of independent loads into shared memory; then each half CTA
+// merges pairs of blocks (loads of both in flight), so a block costs the
+// round trips of its sums and voxels only.  Spans first, first + step, ...
+// (single: only the first).
+constexpr int kSpan = 32;
+
+struct SpanSmem {
+  int pool[kSpan];
+  int scan[kSpan];
+  int skip[kSpan];
+};
+
+__device__ void merge_wave(const BatchDev& b, int w, const int* nt_prefix, int first, int step, bool single,
+                           SpanSmem* sp) {
   const int tid = threadIdx.x;
-  const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
-  const int nt_total = nt_prefix[s1 - s0];
+  const int s0 = b.wave_begin[w], ns = b.wave_begin[w + 1] - s0;
+  const int nt_total = nt_prefix[ns];
   const int half = tid >> 7, sub = tid & (kMergeThreads - 1);
-  for (int item = first_item;; item += step) {
-    const int j = 4 * item + 2 * half;
-    if (j >= nt_total) break;
-    const int q = find_scan(nt_prefix, 0, s1 - s0, j);
-    const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
-    const bool skip = *((volatile int32_t*)m.frame_err) != 0;
-    const int lj = j - nt_prefix[q];
-    const bool pair = j + 1 < nt_prefix[q + 1];
-    int merged = m.storage == 0 ? merge_two<0>(m, lj, pair ? lj + 1 : -1, skip, sub)
-                                : merge_two<1>(m, lj, pair ? lj + 1 : -1, skip, sub);
-    unsigned long long c = merged;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
-    if (!pair && j + 1 < nt_total) {   // the next block starts the next submap
-      const int q3 = find_scan(nt_prefix, 0, s1 - s0, j + 1);
-      const SubmapDev& m2 = view(b, b.scan_map[s0 + q3], w);
-      const bool skip2 = *((volatile int32_t*)m2.frame_err) != 0;
-      merged = m2.storage == 0 ? merge_two<0>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub)
-                               : merge_two<1>(m2, j + 1 - nt_prefix[q3], -1, skip2, sub);
-      c = merged;
+  for (int span = first;; span += step) {
+    const int g0 = span * kSpan;
+    if (g0 >= nt_total) break;
+    const int n = min(kSpan, nt_total - g0);
+    if (tid < n) {
+      const int q = find_scan(nt_prefix, 0, ns, g0 + tid);
+      const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
+      sp->pool[tid] = m.touched[g0 + tid - nt_prefix[q]];
+      sp->scan[tid] = q;
+      sp->skip[tid] = *((volatile int32_t*)m.frame_err) != 0;
+    }
+    __syncthreads();
+    for (int k = 2 * half; k < n; k += 4) {
+      const int q = sp->scan[k];
+      const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
+      const bool pair = k + 1 < n && sp->scan[k + 1] == q;   // a pair shares one submap
+      int merged = m.storage == 0 ? merge_pools<0>(m, sp->pool[k], pair ? sp->pool[k + 1] : -1, sp->skip[k], sub)
+                                  : merge_pools<1>(m, sp->pool[k], pair ? sp->pool[k + 1] : -1, sp->skip[k], sub);
+      unsigned long long c = merged;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if ((tid & 31) == 0 && c) atomicAdd(&m2.st->voxels_merged, c);
+      if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
+      if (!pair && k + 1 < n) {   // the next block starts the next submap
+        const SubmapDev& m2 = view(b, b.scan_map[s0 + sp->scan[k + 1]], w);
+        merged = m2.storage == 0 ? merge_pools<0>(m2, sp->pool[k + 1], -1, sp->skip[k + 1], sub)
+                                 : merge_pools<1>(m2, sp->pool[k + 1], -1, sp->skip[k + 1], sub);
+        c = merged;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if ((tid & 31) == 0 && c) atomicAdd(&m2.st->voxels_merged, c);
+      }
     }
+    __syncthreads();   // the span's shared arrays are rewritten next
     if (single) break;
   }
 }
@@ -179,6 +199,7 @@ template <int kVariant>
 __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int nt_prefix[kMaxWaveScans + 1];
+  __shared__ SpanSmem span;
   stamp(b, 0);
   if (!b.pipelined) {
     for (int w = 0; w < b.n_waves; ++w) {
@@ -194,7 +215,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
       stamp(b, 3 * w + 1);
       // phase 2: merge every touched block of every submap of the wave
       wave_touched(b, w, nt_prefix);
-      merge_wave(b, w, nt_prefix, blockIdx.x, gridDim.x, false);
+      merge_wave(b, w, nt_prefix, blockIdx.x, gridDim.x, false, &span);
       if (!grid_barrier(b)) return;
       stamp(b, 3 * w + 2);
       // phase 3: per-submap bookkeeping of this frame
@@ -215,19 +236,19 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
       t0 = b.tile_prefix[s0];
       n_tiles = b.tile_prefix[s1] - t0;
     }
-    int n_pairs = 0;
+    int n_spans = 0;
     if (w > 0) {
       wave_touched(b, w - 1, nt_prefix);
-      n_pairs = (nt_prefix[b.wave_begin[w] - b.wave_begin[w - 1]] + 3) / 4;   // 4 blocks per CTA item
+      n_spans = (nt_prefix[b.wave_begin[w] - b.wave_begin[w - 1]] + kSpan - 1) / kSpan;   // merge spans
     }
-    const int items = n_tiles + n_pairs;
+    const int items = n_tiles + n_spans;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
       if (it < n_tiles) {
         const int s = find_scan(b.tile_prefix, s0, s1, t0 + it);
         integrate_tile_v<kVariant>(view(b, b.scan_map[s], w), b.scans[s], t0 + it - b.tile_prefix[s], smem,
                                    b.scan_lb[s]);
       } else {
-        merge_wave(b, w - 1, nt_prefix, it - n_tiles, 1, true);   // one item: 4 blocks
+        merge_wave(b, w - 1, nt_prefix, it - n_tiles, 1, true, &span);   // one item: a span
       }
     }
     if (!grid_barrier(b)) return;

@@ -98,6 +98,12 @@ __device__ inline int global_activate(const SubmapDev& m, unsigned long long key
   return -1;
 }
 
+// (a, b) added to a float2 in global memory by the L2, fire and forget: a
+// vector reduction that returns nothing, so no warp waits on it.
+__device__ __forceinline__ void red_add2(float2* addr, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
 // Pool index of an already activated block (read-only probe), or -1.
 __device__ __forceinline__ int find_pool(const SubmapDev& m, unsigned long long key) {
   const int s = hash_find(m, key);
@@ -394,7 +400,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
         fixed_add(t.lo_wd + e, t.hi_wd + e, fx.S, __float2ll_rn(w * dc * fx.scale));
         fixed_add(t.lo_w + e, t.hi_w + e, fx.S, __float2ll_rn(w * fx.scale));
       } else if (gpool >= 0) {
-        atomicAdd(m.acc + (size_t)gpool * kVoxPerBlock + l, make_float2(w * dc, w));
+        red_add2(m.acc + (size_t)gpool * kVoxPerBlock + l, w * dc, w);
       }
       if (d.left == 0) break;
       // next axis: the traversal rule of Dda::step, as selects
@@ -445,7 +451,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
         if ((t.lo_w[e] | (unsigned)t.hi_w[e]) == 0u) continue;
         const float w = fixed_value(t.lo_w[e], t.hi_w[e], fx.S, fx.inv_scale);
         const float wd = fixed_value(t.lo_wd[e], t.hi_wd[e], fx.S, fx.inv_scale);
-        if (w != 0.0f) atomicAdd(dst + v, make_float2(wd, w));
+        if (w != 0.0f) red_add2(dst + v, wd, w);
       }
     }
   }
@@ -548,9 +554,16 @@ struct Vox4<1> {   // FP16 storage: D / trunc and W as IEEE half, FP32 arithmeti
 // loads of both blocks are issued before any result is used, so two blocks'
 // dependent chains overlap.  Returns the voxels merged by this thread.
 template <int kStore>
+__device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, bool skip, int tid);
+
+template <int kStore>
 __device__ __forceinline__ int merge_two(const SubmapDev& m, int j0, int j1, bool skip, int tid) {
-  const int p0 = m.touched[j0];
-  const int p1 = j1 >= 0 ? m.touched[j1] : -1;
+  return merge_pools<kStore>(m, m.touched[j0], j1 >= 0 ? m.touched[j1] : -1, skip, tid);
+}
+
+// The same for blocks given by pool index (p1 < 0: none).
+template <int kStore>
+__device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, bool skip, int tid) {
   float4* a = reinterpret_cast<float4*>(m.acc + (size_t)p0 * kVoxPerBlock) + 2 * tid;
   float4* b = p1 >= 0 ? reinterpret_cast<float4*>(m.acc + (size_t)p1 * kVoxPerBlock) + 2 * tid : nullptr;
   const float4 a0 = a[0], a1 = a[1];
