@@ -50,6 +50,13 @@ template <int kStore>
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
   __shared__ int head[2];
   __shared__ unsigned long long red[kMergeThreads / 32];
+  // The first pair's pool indices, read before the scan's block count is
+  // known (entries past it are stale but in bounds and unused): their round
+  // trip overlaps the one of the count.
+  const int g = (int)gridDim.x;
+  const int j_first = blockIdx.x;
+  const int p_first0 = j_first < m.max_blocks ? m.touched[j_first] : -1;
+  const int p_first1 = j_first + g < m.max_blocks ? m.touched[j_first + g] : -1;
   if (threadIdx.x == 0) {
     // Read the scan's touched-block count and error bits, then take a ticket
     // (the fence orders the reads first; nothing is in flight yet).  The CTA
@@ -76,8 +83,8 @@ __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
   const bool skip = head[1] != 0;
   const int tid = threadIdx.x;
   unsigned long long merged = 0;
-  const int g = (int)gridDim.x;
-  for (int j = blockIdx.x; j < nt; j += 2 * g) {
+  if (j_first < nt) merged += merge_pools<kStore>(m, p_first0, j_first + g < nt ? p_first1 : -1, skip, tid);
+  for (int j = j_first + 2 * g; j < nt; j += 2 * g) {
     const int j1 = j + g < nt ? j + g : -1;
     merged += merge_two<kStore>(m, j, j1, skip, tid);
   }

@@ -176,7 +176,7 @@ __device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
   return ((uint32_t)key ^ (uint32_t)(key >> 29)) * 0x9E3779B1u;
 }
 
-constexpr int kCache = 64;          // block -> pool cache entries per CTA
+constexpr int kCache = 256;         // block -> pool cache entries per CTA (power of two)
 constexpr int kCachePending = -2;
 
 // Shared per-voxel sums are exact 64-bit fixed point X = hi * 2^S + lo held
@@ -266,7 +266,7 @@ __device__ __forceinline__ float fixed_value(unsigned lo, int hi, int S, float i
 // idempotent), so nobody waits.
 __device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t, unsigned long long key,
                                            uint32_t ep) {
-  const uint32_t h = slot_hash(key) >> 26;
+  const uint32_t h = slot_hash(key) >> 24;
   for (int p = 0; p < 8; ++p) {
     const int q = (h + p) & (kCache - 1);
     unsigned long long cur = *((volatile unsigned long long*)(t.ckey + q));
