@@ -178,6 +178,7 @@ __device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
 
 constexpr int kCache = 256;         // block -> pool cache entries per CTA (power of two)
 constexpr int kCachePending = -2;
+constexpr int kCacheWait = 4096;    // polls of a pending cache entry before activating anyway
 
 // Shared per-voxel sums are exact 64-bit fixed point X = hi * 2^S + lo held
 // in two 32-bit words (lo unsigned, < 2^S per observation; hi signed), so
@@ -262,8 +263,8 @@ __device__ __forceinline__ float fixed_value(unsigned lo, int hi, int S, float i
 
 // Pool index of a block through the CTA's block -> pool cache.  The first
 // thread to meet a block activates it and publishes the index; a thread that
-// finds the entry still pending activates it itself (activation is
-// idempotent), so nobody waits.
+// finds the entry pending waits for it (bounded, then activates the block
+// itself: activation is idempotent).
 __device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t, unsigned long long key,
                                            uint32_t ep) {
   const uint32_t h = slot_hash(key) >> 24;
@@ -281,7 +282,15 @@ __device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t
       return pool;
     }
     if (cur == key) {
-      const int pool = *((volatile int*)(t.cpool + q));
+      // Another thread of the CTA is activating the block: wait for its
+      // answer in shared memory (a few hundred cycles) rather than repeat the
+      // global activation, whose loads and epoch CAS would all hit one slot.
+      // Bounded: after the limit the thread activates the block itself.
+      int pool = *((volatile int*)(t.cpool + q));
+      for (int it = 0; pool == kCachePending && it < kCacheWait; ++it) {
+        __nanosleep(32);
+        pool = *((volatile int*)(t.cpool + q));
+      }
       return pool != kCachePending ? pool : global_activate(m, key, ep);
     }
   }
