@@ -35,15 +35,17 @@ KERNEL_SOURCES = ("paper_2410_21149_gb300/csrc/covox_dev.cuh", "paper_2410_21149
                   "paper_2410_21149_gb300/csrc/integrate.cu")
 
 
-def kernel_traffic(name: str):
-    """DRAM bytes per launch from the committed ncu summary, or None if the
-    kernel sources changed since it was captured."""
+def kernel_traffic(name: str, ppc: int = 0, lb: int = 0):
+    """DRAM bytes per launch from the committed ncu summary for this kernel
+    and launch shape, or None if there is none or the kernel sources changed
+    since it was captured."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
+    name = f"{name}|{ppc},{lb}" if f"{name}|{ppc},{lb}" in t else name
     if name not in t:
         return None
     h = hashlib.sha256()
@@ -536,7 +538,7 @@ def run_ours(args):
                                    "speedup_vs_fp32": sec32 / sec16, "sdf_rmse_m": rmse16,
                                    "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof16.items() if v[1]}}},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": kernel_traffic(dom), "peak_source": peak_src,
+                     "frac": achieved / hbm, "traffic": kernel_traffic(dom, args.ppc, args.lb), "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms},
         "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / hbm},
         "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
