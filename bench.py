@@ -540,7 +540,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": kernel_traffic(dom, args.ppc, args.lb), "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms},
-        "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / hbm},
+        "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / hbm,
+                          "block_granular_bytes_per_step": 2 * S32 * 512 * blocks},
         "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
         "kernel_share": {k: v[0] / sum(x[0] for x in prof.values()) for k, v in prof.items() if v[1]},
         "e2e": {"value": tot_valid / (e2e_ms / 1e3 / args.steps), "unit": "points/s",
@@ -687,6 +688,7 @@ def run_lidar(args, ws, rank, peaks, peak_src):
                      "algorithmic_bytes_per_launch": r["kernel_bytes"], "avg_launch_ms": r["batched_kernel_ms"]},
         "counts_per_step": {k: r[k] for k in ("points", "observations", "voxels_merged", "blocks_touched",
                                               "blocks_allocated")},
+        "block_granular_bytes_per_step": 2 * 8 * 512 * r["blocks_touched"],
         "autotuned": r["tuned"], "batched_phases": r["phases"],
         "e2e": {"value": pts / (r["e2e_ms_per_step"] / 1e3), "unit": "points/s",
                 "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"]},
