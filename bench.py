@@ -552,6 +552,7 @@ def run_ours(args):
         "gpu_launches_per_step": launches_per_step,
         "clocks": clk,
     }
+    out["forms"]["esdf"] = esdf_form(sub32, stream, args, peaks)
     if not args.no_learned:
         out["forms"]["learned_weight"] = learned_form(wl, pts, Ts, stream, args, ws, rmse32, ms32 / args.steps)
     if not args.no_batched:
@@ -576,6 +577,39 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def esdf_form(sub, stream, args, peaks):
+    """Distance field of the integrated multiroom submap (Sec. III-E): time of
+    one cvx_compute_esdf call (CUDA events, best of K after W warm-ups), the
+    box it sweeps, and its algorithmic bytes: 4 B per box voxel to initialise
+    the grid, 8 B per box voxel and axis pass (read + write), 8 B per
+    allocated voxel to read D and W, 4 B per allocated voxel written."""
+    import torch
+    with torch.cuda.stream(stream):
+        keys = sub.extract(stream)[0]
+        nb = int(keys.shape[0])
+        for _ in range(args.warmup):
+            sub.esdf(stream=stream)
+        ts = []
+        for _ in range(max(args.steps, 3)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sub.esdf(stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    k = keys.cpu().numpy()
+    box = ((k.max(0) - k.min(0) + 1) * 8).astype(np.int64)
+    V, N = int(np.prod(box)), nb * 512
+    ms = min(ts)
+    nbytes = 4 * V + 3 * 8 * V + 8 * N + 4 * N
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    return {"ms": ms, "blocks": nb, "box_voxels": V, "box": box.tolist(),
+            "voxels_out_per_s": N / (ms / 1e3), "box_voxels_per_s": V / (ms / 1e3),
+            "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (ms / 1e3) / 1e9,
+            "frac_hbm": nbytes / (ms / 1e3) / 1e9 / hbm,
+            "site_rule": "W > 0 and |D| <= voxel size; capped at 2 m"}
 
 
 def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):

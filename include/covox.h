@@ -168,6 +168,23 @@ cvx_status cvx_submap_status(cvx_submap* map);
  * pending scan first). */
 cvx_status cvx_submap_counters(cvx_submap* map, cvx_counters* out);
 
+/* Euclidean distance field of the submap (Sec. III-E builds an ESDF from the
+ * TSDF blocks; the paper fixes neither the site rule nor a cap, this is the
+ * library's reading).  For every voxel of every allocated block, in the
+ * block order of cvx_extract_blocks(): out = voxel_size * the distance, in
+ * voxel units, from its centre to the centre of the nearest site voxel,
+ * capped at max_dist (max_dist when the submap has no site); sites are the
+ * allocated voxels with W > w_min and |D| <= site_band (metres).  Unsigned.
+ * out: device float32 [n_blocks, 512]; sq_dist: device int32 [n_blocks, 512]
+ * of the exact squared distances in voxel units (-1: no site), or NULL.
+ * Computed from scratch over the box spanned by the allocated blocks (a
+ * pipelined submap's pending scan is merged first); scratch of 24 B per box
+ * voxel comes from the submap's allocator.  CVX_ERR_CAPACITY if the box
+ * exceeds 16,384 voxels on an axis, CVX_ERR_OOM if the scratch cannot be
+ * allocated.  Synchronises `stream` once (to size the box). */
+cvx_status cvx_compute_esdf(cvx_submap* map, float site_band, float w_min, float max_dist, float* out,
+                            int32_t* sq_dist, void* stream);
+
 /* Free the submap and everything it allocated (synchronises its stream). */
 void cvx_destroy(cvx_submap* map);
 

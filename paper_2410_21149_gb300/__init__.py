@@ -85,6 +85,19 @@ class Submap:
     def reset(self, stream=None) -> None:
         _capi.cvx_reset_submap(self.handle, stream)
 
+    def esdf(self, site_band: Optional[float] = None, w_min: float = 0.0, max_dist: float = 2.0,
+             exact_sq: bool = False, stream=None):
+        """Distance field of the allocated voxels ([nb, 512] float32 CUDA tensor in
+        extract() block order; with exact_sq also the int32 squared distances in
+        voxel units).  site_band defaults to the voxel size."""
+        import torch
+        nb = self.num_blocks(stream)
+        out = torch.empty((max(nb, 1), 512), dtype=torch.float32, device="cuda")
+        sq = torch.empty((max(nb, 1), 512), dtype=torch.int32, device="cuda") if exact_sq else None
+        band = self.voxel_size if site_band is None else site_band
+        _capi.cvx_compute_esdf(self.handle, band, w_min, max_dist, out, sq, stream)
+        return (out[:nb], sq[:nb]) if exact_sq else out[:nb]
+
     def flush(self, stream=None) -> None:
         """Merge the scan a pipelined submap left pending (no-op otherwise)."""
         _capi.cvx_flush_submap(self.handle, stream)

@@ -91,6 +91,7 @@ SIGNATURES = {
     "cvx_reset_submap": (_i32, [_vp, _vp]),
     "cvx_submap_status": (_i32, [_vp]),
     "cvx_flush_submap": (_i32, [_vp, _vp]),
+    "cvx_compute_esdf": (_i32, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
     "cvx_submap_counters": (_i32, [_vp, ctypes.POINTER(cvx_counters)]),
     "cvx_destroy": (None, [_vp]),
     "cvx_integrate_scan_noalloc": (_i32, [ctypes.POINTER(cvx_submap_view), _vp, _i64, _vp, _vp,
@@ -246,6 +247,16 @@ def cvx_extract_blocks(handle: int, capacity: int, keys, dist, weight, stream=No
 
 def cvx_reset_submap(handle: int, stream=None) -> None:
     check(lib().cvx_reset_submap(handle, _stream_handle(stream)), "cvx_reset_submap")
+
+
+def cvx_compute_esdf(handle: int, site_band: float, w_min: float, max_dist: float, out, sq_dist=None,
+                     stream=None) -> None:
+    """out: float32 CUDA tensor [n_blocks, 512]; sq_dist: int32 CUDA tensor of the
+    same shape or None."""
+    o = _dev_ptr(out, "torch.float32", "out")
+    q = _dev_ptr(sq_dist, "torch.int32", "sq_dist") if sq_dist is not None else None
+    check(lib().cvx_compute_esdf(handle, float(site_band), float(w_min), float(max_dist), o, q,
+                                 _stream_handle(stream)), "cvx_compute_esdf")
 
 
 def cvx_flush_submap(handle: int, stream=None) -> None:

@@ -1,0 +1,247 @@
+// esdf.cu -- Euclidean distance field of a submap (coVoxSLAM Sec. III-E).
+//
+// For every voxel of every allocated block: the distance between its centre
+// and the centre of the nearest site voxel (W > w_min and |D| <= site_band),
+// capped at max_dist.  The paper updates its ESDF incrementally with
+// per-block queues and Parallel Banding (PBA) sweeps; this library computes
+// the same exact field from scratch for a whole submap:
+//   esdf_bbox_kernel   the voxel box spanned by the allocated blocks;
+//   esdf_sites_kernel  sites marked 0 in a dense int32 grid of the box (the
+//                      rest stays "far");
+//   esdf_pass_kernel   one pass per axis, one thread per grid line: the lower
+//                      envelope of the parabolas (q - p)^2 + f(p) of the
+//                      line's finite entries, intersections compared as
+//                      exact integer fractions, so each pass returns the
+//                      exact minimum (squared distances in voxel units);
+//   esdf_out_kernel    gather into the blocks' [n_blocks, 512] layout.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "../../include/covox.h"
+#include "covox_dev.cuh"
+#include "prof.h"
+#include "submap.h"
+
+using namespace covox;
+
+namespace {
+
+constexpr int32_t kFar = 0x7f7f7f7f;       // memset byte 0x7f: no site on the line (yet)
+constexpr int kMaxAxis = 16384;            // voxels per box axis: 3 * 16383^2 + 16383^2 < kFar
+
+__global__ void esdf_bbox_kernel(const int32_t* __restrict__ block_keys, int nb, int* box) {
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int k = block_keys[3 * b + c];
+      mn[c] = min(mn[c], k);
+      mx[c] = max(mx[c], k);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mn[c] = __reduce_min_sync(0xffffffffu, mn[c]);
+    mx[c] = __reduce_max_sync(0xffffffffu, mx[c]);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      atomicMin(box + c, mn[c]);
+      atomicMax(box + 3 + c, mx[c]);
+    }
+  }
+}
+
+__global__ void esdf_box_init_kernel(int* box) {
+  if (threadIdx.x < 3) {
+    box[threadIdx.x] = INT_MAX;
+    box[3 + threadIdx.x] = INT_MIN;
+  }
+}
+
+struct Box {
+  int lo[3];    // lowest voxel index
+  int n[3];     // extents in voxels
+};
+
+__device__ __forceinline__ size_t grid_index(const Box& bx, int v0, int v1, int v2) {
+  return (size_t)(v0 - bx.lo[0]) + (size_t)bx.n[0] * ((size_t)(v1 - bx.lo[1]) + (size_t)bx.n[1] * (v2 - bx.lo[2]));
+}
+
+__global__ void esdf_sites_kernel(SubmapDev m, int nb, Box bx, float site_band, float w_min,
+                                  int32_t* __restrict__ grid) {
+  const size_t total = (size_t)nb * kVoxPerBlock;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / kVoxPerBlock), l = (int)(e % kVoxPerBlock);
+    float D, W;
+    if (m.storage == CVX_STORE_F32) {
+      D = ((const float*)m.D)[e];
+      W = ((const float*)m.W)[e];
+    } else {
+      D = __half2float(((const __half*)m.D)[e]) * m.trunc;
+      W = __half2float(((const __half*)m.W)[e]);
+    }
+    if (!(W > w_min && fabsf(D) <= site_band)) continue;
+    const int v0 = m.block_keys[3 * b] * 8 + (l & 7);
+    const int v1 = m.block_keys[3 * b + 1] * 8 + ((l >> 3) & 7);
+    const int v2 = m.block_keys[3 * b + 2] * 8 + (l >> 6);
+    grid[grid_index(bx, v0, v1, v2)] = 0;
+  }
+}
+
+// Line L of a pass: start base + q * se for q < n; scratch element k of the
+// line at k * lines + L (adjacent lines adjacent in memory).
+struct Pass {
+  int n, lines, c0;
+  long long s0, s1, se;
+};
+
+__global__ void esdf_pass_kernel(int32_t* __restrict__ grid, Pass ps, int32_t* __restrict__ sv,
+                                 int32_t* __restrict__ sf, long long* __restrict__ szn, int32_t* __restrict__ szd) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= ps.lines) return;
+  const size_t lines = (size_t)ps.lines;
+  const long long base = (long long)(L % ps.c0) * ps.s0 + (long long)(L / ps.c0) * ps.s1;
+  // envelope: vertices v[0..k], their values f, left interval bounds z = zn / zd (z[0] = -inf: zd = 0)
+  int k = -1;
+  for (int q = 0; q < ps.n; ++q) {
+    const int32_t fq = grid[base + q * ps.se];
+    if (fq >= kFar) continue;
+    const long long Fq = (long long)fq + (long long)q * q;
+    long long num = 0;
+    int den = 0;
+    while (k >= 0) {
+      const size_t at = (size_t)k * lines + L;
+      const int p = sv[at];
+      num = Fq - ((long long)sf[at] + (long long)p * p);   // parabolas of p and q meet at num / den
+      den = 2 * (q - p);
+      const int zdk = szd[at];
+      if (zdk == 0 || num * zdk > szn[at] * den) break;     // meets right of z[k]: keep p
+      --k;
+    }
+    ++k;
+    const size_t at = (size_t)k * lines + L;
+    sv[at] = q;
+    sf[at] = fq;
+    szn[at] = k == 0 ? 0 : num;
+    szd[at] = k == 0 ? 0 : den;
+  }
+  if (k < 0) return;   // no finite entry: the line stays far
+  const int K = k;
+  k = 0;
+  for (int q = 0; q < ps.n; ++q) {
+    while (k < K) {
+      const size_t nx = (size_t)(k + 1) * lines + L;
+      if (szn[nx] > (long long)q * szd[nx]) break;   // z[k+1] > q
+      ++k;
+    }
+    const size_t at = (size_t)k * lines + L;
+    const long long d = (long long)(q - sv[at]) * (q - sv[at]) + sf[at];
+    grid[base + q * ps.se] = (int32_t)d;   // < kFar by the box limit
+  }
+}
+
+__global__ void esdf_out_kernel(SubmapDev m, int nb, Box bx, const int32_t* __restrict__ grid, float vs,
+                                float max_dist, float* __restrict__ out, int32_t* __restrict__ sq) {
+  const size_t total = (size_t)nb * kVoxPerBlock;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e / kVoxPerBlock), l = (int)(e % kVoxPerBlock);
+    const int v0 = m.block_keys[3 * b] * 8 + (l & 7);
+    const int v1 = m.block_keys[3 * b + 1] * 8 + ((l >> 3) & 7);
+    const int v2 = m.block_keys[3 * b + 2] * 8 + (l >> 6);
+    const int32_t g = grid[grid_index(bx, v0, v1, v2)];
+    if (sq) sq[e] = g >= kFar ? -1 : g;
+    out[e] = g >= kFar ? max_dist : fminf(__fsqrt_rn((float)g) * vs, max_dist);
+  }
+}
+
+void* scratch_alloc(cvx_submap* map, size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  if (map->p.alloc) return map->p.alloc(bytes, s, map->p.alloc_ctx);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void scratch_free(cvx_submap* map, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (map->p.free) map->p.free(p, bytes, s, map->p.alloc_ctx);
+  else if (!map->p.alloc) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" cvx_status cvx_compute_esdf(cvx_submap* map, float site_band, float w_min, float max_dist,
+                                       float* out, int32_t* sq_dist, void* stream) {
+  if (!map || !out) return CVX_ERR_INVALID_ARG;
+  if (!(site_band >= 0) || !std::isfinite(site_band) || !(w_min >= 0) || !std::isfinite(w_min) ||
+      !(max_dist > 0) || !std::isfinite(max_dist))
+    return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  map->last_stream = s;
+  if (flush_pending(map, s, false) != CVX_OK) return CVX_ERR_CUDA;
+  int32_t nb32 = 0;
+  if (cudaMemcpyAsync(&nb32, &map->dev.st->n_blocks, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  const int nb = std::min<int32_t>(nb32, map->dev.max_blocks);
+  if (nb <= 0) return CVX_OK;
+  const SubmapDev& m = map->dev;
+  // block box (6 ints)
+  int* box = (int*)scratch_alloc(map, 64, s);
+  if (!box) return CVX_ERR_OOM;
+  int hb[6];
+  COVOX_LAUNCH(kKEsdf, s, esdf_box_init_kernel<<<1, 32, 0, s>>>(box));
+  COVOX_LAUNCH(kKEsdf, s, esdf_bbox_kernel<<<std::min(num_sms() * 4, (nb + 255) / 256), 256, 0, s>>>(
+                              m.block_keys, nb, box));
+  const bool ok = cudaMemcpyAsync(hb, box, sizeof(hb), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                  cudaStreamSynchronize(s) == cudaSuccess;
+  scratch_free(map, box, 64, s);
+  if (!ok) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  Box bx;
+  size_t voxels = 1;
+  for (int c = 0; c < 3; ++c) {
+    bx.lo[c] = hb[c] * 8;
+    const long long n = ((long long)hb[3 + c] - hb[c] + 1) * 8;
+    if (n > kMaxAxis) return CVX_ERR_CAPACITY;   // beyond the exact int32 range of the passes
+    bx.n[c] = (int)n;
+    voxels *= (size_t)n;
+  }
+  // dense grid and per-line envelope scratch (20 B per grid voxel)
+  const size_t grid_bytes = voxels * 4, scr_bytes = voxels * 20;
+  char* mem = (char*)scratch_alloc(map, grid_bytes + scr_bytes, s);
+  if (!mem) return CVX_ERR_OOM;
+  int32_t* grid = (int32_t*)mem;
+  long long* szn = (long long*)(mem + grid_bytes);
+  int32_t* sv = (int32_t*)(mem + grid_bytes + voxels * 8);
+  int32_t* sf = (int32_t*)(mem + grid_bytes + voxels * 12);
+  int32_t* szd = (int32_t*)(mem + grid_bytes + voxels * 16);
+  cudaMemsetAsync(grid, 0x7f, grid_bytes, s);
+  const int g1 = num_sms() * 8;
+  COVOX_LAUNCH(kKEsdf, s, esdf_sites_kernel<<<g1, 256, 0, s>>>(m, nb, bx, site_band, w_min, grid));
+  const long long nx = bx.n[0], ny = bx.n[1], nz = bx.n[2];
+  const Pass passes[3] = {
+      {(int)nx, (int)(ny * nz), (int)ny, nx, nx * ny, 1},        // x lines: y + ny z
+      {(int)ny, (int)(nx * nz), (int)nx, 1, nx * ny, nx},        // y lines: x + nx z
+      {(int)nz, (int)(nx * ny), (int)nx, 1, nx, nx * ny},        // z lines: x + nx y
+  };
+  for (const Pass& ps : passes)
+    COVOX_LAUNCH(kKEsdf, s, esdf_pass_kernel<<<(ps.lines + 127) / 128, 128, 0, s>>>(grid, ps, sv, sf, szn, szd));
+  COVOX_LAUNCH(kKEsdf, s, esdf_out_kernel<<<g1, 256, 0, s>>>(m, nb, bx, grid, map->p.voxel_size, max_dist,
+                                                              out, sq_dist));
+  const bool launched = cudaGetLastError() == cudaSuccess;
+  scratch_free(map, mem, grid_bytes + scr_bytes, s);
+  return launched ? CVX_OK : CVX_ERR_CUDA;
+}

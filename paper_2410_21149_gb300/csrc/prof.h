@@ -21,7 +21,8 @@ enum KernelKind : int {
   kKPipelined = 10, // pipelined per-scan kernel (tiles + merges of the previous scan)
   kKFlush = 11,     // merge of a pipelined submap's pending scan
   kKPipeClose = 12, // pipelined per-scan bookkeeping after each scan
-  kNumKinds = 13
+  kKEsdf = 13,      // distance field of a submap
+  kNumKinds = 14
 };
 
 void prof_begin(int kind, cudaStream_t s);
