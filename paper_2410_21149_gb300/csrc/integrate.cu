@@ -345,7 +345,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   int expect = 9;
   m->pipelined = (p->flags & CVX_SUBMAP_PIPELINED) != 0;
   SubmapDev& db = m->dev_b;
-  if (m->pipelined) {   // second per-scan set: sums, touch map, touched list
+  if (m->pipelined) {   // second per-scan set: sums and touched list
     db.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
     db.touched = (int32_t*)sub_alloc(m, nb * 4);
     expect = 11;
