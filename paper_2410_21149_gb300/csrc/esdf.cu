@@ -8,7 +8,9 @@
 //   esdf_bbox_kernel   the voxel box spanned by the allocated blocks;
 //   esdf_sites_kernel  sites marked 0 in a dense int32 grid of the box (the
 //                      rest stays "far");
-//   esdf_pass_kernel   one pass per axis, one thread per grid line: the lower
+//   esdf_first_pass_kernel  x lines: squared distance to the line's nearest
+//                      site, one sweep each way;
+//   esdf_pass_kernel   y then z lines, one thread per line: the lower
 //                      envelope of the parabolas (q - p)^2 + f(p) of the
 //                      line's finite entries, intersections compared as
 //                      exact integer fractions, so each pass returns the
@@ -146,6 +148,30 @@ __global__ void esdf_pass_kernel(int32_t* __restrict__ grid, Pass ps, int32_t* _
   }
 }
 
+// First pass (x lines, sites 0, the rest far): the squared distance to the
+// nearest site of the line by one sweep each way; no envelope needed.
+__global__ void esdf_first_pass_kernel(int32_t* __restrict__ grid, Pass ps) {
+  const int L = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= ps.lines) return;
+  const long long base = (long long)(L % ps.c0) * ps.s0 + (long long)(L / ps.c0) * ps.s1;
+  int last = INT_MIN;
+  for (int q = 0; q < ps.n; ++q) {
+    int32_t* g = grid + base + q * ps.se;
+    if (*g == 0) last = q;
+    else if (last != INT_MIN) *g = (q - last) * (q - last);
+  }
+  int next = INT_MIN;
+  for (int q = ps.n - 1; q >= 0; --q) {
+    int32_t* g = grid + base + q * ps.se;
+    if (*g == 0) {
+      next = q;
+    } else if (next != INT_MIN) {
+      const int32_t d = (next - q) * (next - q);
+      if (d < *g) *g = d;
+    }
+  }
+}
+
 __global__ void esdf_out_kernel(SubmapDev m, int nb, Box bx, const int32_t* __restrict__ grid, float vs,
                                 float max_dist, float* __restrict__ out, int32_t* __restrict__ sq) {
   const size_t total = (size_t)nb * kVoxPerBlock;
@@ -237,8 +263,11 @@ extern "C" cvx_status cvx_compute_esdf(cvx_submap* map, float site_band, float w
       {(int)ny, (int)(nx * nz), (int)nx, 1, nx * ny, nx},        // y lines: x + nx z
       {(int)nz, (int)(nx * ny), (int)nx, 1, nx, nx * ny},        // z lines: x + nx y
   };
-  for (const Pass& ps : passes)
-    COVOX_LAUNCH(kKEsdf, s, esdf_pass_kernel<<<(ps.lines + 127) / 128, 128, 0, s>>>(grid, ps, sv, sf, szn, szd));
+  // x: sites only (two sweeps); y and z: envelopes (adjacent threads read adjacent voxels)
+  COVOX_LAUNCH(kKEsdf, s, esdf_first_pass_kernel<<<(passes[0].lines + 127) / 128, 128, 0, s>>>(grid, passes[0]));
+  for (int a = 1; a < 3; ++a)
+    COVOX_LAUNCH(kKEsdf, s, esdf_pass_kernel<<<(passes[a].lines + 127) / 128, 128, 0, s>>>(grid, passes[a], sv, sf,
+                                                                                            szn, szd));
   COVOX_LAUNCH(kKEsdf, s, esdf_out_kernel<<<g1, 256, 0, s>>>(m, nb, bx, grid, map->p.voxel_size, max_dist,
                                                               out, sq_dist));
   const bool launched = cudaGetLastError() == cudaSuccess;
