@@ -553,6 +553,7 @@ def run_ours(args):
         "clocks": clk,
     }
     out["forms"]["esdf"] = esdf_form(sub32, stream, args, peaks)
+    out["forms"]["hash_stress"] = hash_stress_form(args)
     if not args.no_learned:
         out["forms"]["learned_weight"] = learned_form(wl, pts, Ts, stream, args, ws, rmse32, ms32 / args.steps)
     if not args.no_batched:
@@ -610,6 +611,43 @@ def esdf_form(sub, stream, args, peaks):
             "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (ms / 1e3) / 1e9,
             "frac_hbm": nbytes / (ms / 1e3) / 1e9 / hbm,
             "site_rule": "W > 0 and |D| <= voxel size; capped at 2 m"}
+
+
+def hash_stress_form(args, slots_log2=26, load_factors=(0.1, 0.5, 0.85)):
+    """The block hash alone (the paper's hash stress test: tens of millions of
+    insertions): seeded random block keys (uniform in +-2^19 per axis,
+    duplicates allowed) inserted into an empty table of 2^26 slots at each
+    load factor, then looked up; best of K timings (CUDA events), table
+    cleared between runs."""
+    import torch
+    from paper_2410_21149_gb300 import _capi
+    slots = 1 << slots_log2
+    res = {"slots": slots, "key_distribution": "uniform int32 in [-2^19, 2^19) per axis, seeded"}
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1234)
+    for lf in load_factors:
+        n = int(lf * slots)
+        coords = torch.randint(-(1 << 19), 1 << 19, (n, 3), dtype=torch.int32, device="cuda", generator=g)
+        pool = torch.empty(n, dtype=torch.int32, device="cuda")
+        ins, fnd = [], []
+        for _ in range(max(3, min(args.steps, 5))):
+            h = _capi.cvx_block_hash_create(slots, n)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            _capi.cvx_block_hash_insert(h, coords, pool)
+            e1.record()
+            _capi.cvx_block_hash_find(h, coords, pool)
+            e2.record()
+            e2.synchronize()
+            st, nb, _ = _capi.cvx_block_hash_info(h)
+            assert st == 0, st
+            _capi.cvx_block_hash_destroy(h)
+            ins.append(e0.elapsed_time(e1))
+            fnd.append(e1.elapsed_time(e2))
+        res[f"lf{lf}"] = {"keys": n, "distinct": nb, "insert_ms": min(ins), "find_ms": min(fnd),
+                          "inserts_per_s": n / (min(ins) / 1e3), "finds_per_s": n / (min(fnd) / 1e3)}
+        del coords, pool
+    return res
 
 
 def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):

@@ -188,6 +188,34 @@ cvx_status cvx_compute_esdf(cvx_submap* map, float site_band, float w_min, float
 /* Free the submap and everything it allocated (synchronises its stream). */
 void cvx_destroy(cvx_submap* map);
 
+/* ---- the block hash on its own (Sec. III-B "activate"; Sec. IV's hash
+ * stress test inserts tens of millions of keys) ----
+ * The table a submap uses: packed block keys (each coordinate in
+ * [-2^20, 2^20)), open addressing with linear probing (at most 4,096 probes),
+ * keys claimed by 64-bit CAS.  A new key takes the next pool index (blocks
+ * are numbered in allocation order); the new keys of a warp take theirs with
+ * one atomic per warp. */
+typedef struct cvx_block_hash cvx_block_hash;
+
+/* slots: power of two >= 2 (load factor = keys / slots; the table keeps
+ * working up to ~0.85); max_blocks: pool capacity.  Synchronous. */
+cvx_status cvx_block_hash_create(int64_t slots, int64_t max_blocks, cvx_block_hash** out);
+/* Insert-or-find the n blocks of coords (device int32 [n,3]); pool (device
+ * int32 [n]) receives each block's pool index, equal for equal keys, or -1 if
+ * the key could not be placed (capacity, key range: recorded, see _info).
+ * Asynchronous on `stream`. */
+cvx_status cvx_block_hash_insert(cvx_block_hash* hash, const int32_t* coords, int64_t n, int32_t* pool,
+                                 void* stream);
+/* Lookup only: pool[i] = the block's pool index or -1.  Asynchronous. */
+cvx_status cvx_block_hash_find(cvx_block_hash* hash, const int32_t* coords, int64_t n, int32_t* pool,
+                               void* stream);
+/* Number of blocks and, if block_keys != NULL, the first min(n, capacity)
+ * block coordinates in pool order (int32 [.,3], host or device).  Returns the
+ * recorded error (CVX_ERR_CAPACITY, CVX_ERR_KEY_RANGE, CVX_ERR_TIMEOUT) or
+ * CVX_OK.  Synchronises the stream of the last call. */
+cvx_status cvx_block_hash_info(cvx_block_hash* hash, int64_t* n_blocks, int32_t* block_keys, int64_t capacity);
+void cvx_block_hash_destroy(cvx_block_hash* hash);
+
 /* Library version string. */
 const char* cvx_version(void);
 

@@ -91,6 +91,11 @@ SIGNATURES = {
     "cvx_reset_submap": (_i32, [_vp, _vp]),
     "cvx_submap_status": (_i32, [_vp]),
     "cvx_flush_submap": (_i32, [_vp, _vp]),
+    "cvx_block_hash_create": (_i32, [_i64, _i64, _vp]),
+    "cvx_block_hash_insert": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "cvx_block_hash_find": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "cvx_block_hash_info": (_i32, [_vp, _vp, _vp, _i64]),
+    "cvx_block_hash_destroy": (None, [_vp]),
     "cvx_compute_esdf": (_i32, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
     "cvx_submap_counters": (_i32, [_vp, ctypes.POINTER(cvx_counters)]),
     "cvx_destroy": (None, [_vp]),
@@ -257,6 +262,43 @@ def cvx_compute_esdf(handle: int, site_band: float, w_min: float, max_dist: floa
     q = _dev_ptr(sq_dist, "torch.int32", "sq_dist") if sq_dist is not None else None
     check(lib().cvx_compute_esdf(handle, float(site_band), float(w_min), float(max_dist), o, q,
                                  _stream_handle(stream)), "cvx_compute_esdf")
+
+
+def cvx_block_hash_create(slots: int, max_blocks: int) -> int:
+    h = ctypes.c_void_p()
+    check(lib().cvx_block_hash_create(int(slots), int(max_blocks), ctypes.byref(h)), "cvx_block_hash_create")
+    return h.value
+
+
+def cvx_block_hash_insert(handle: int, coords, pool, stream=None) -> None:
+    """coords: int32 CUDA tensor [n,3]; pool: int32 CUDA tensor [n] (output)."""
+    n = int(coords.shape[0])
+    check(lib().cvx_block_hash_insert(handle, _dev_ptr(coords, "torch.int32", "coords") if n else None, n,
+                                      _dev_ptr(pool, "torch.int32", "pool") if n else None,
+                                      _stream_handle(stream)), "cvx_block_hash_insert")
+
+
+def cvx_block_hash_find(handle: int, coords, pool, stream=None) -> None:
+    n = int(coords.shape[0])
+    check(lib().cvx_block_hash_find(handle, _dev_ptr(coords, "torch.int32", "coords") if n else None, n,
+                                    _dev_ptr(pool, "torch.int32", "pool") if n else None,
+                                    _stream_handle(stream)), "cvx_block_hash_find")
+
+
+def cvx_block_hash_info(handle: int, with_keys: bool = False):
+    """(status, n_blocks, block keys int32 [n,3] numpy array or None); synchronous."""
+    nb = ctypes.c_int64(0)
+    st = int(lib().cvx_block_hash_info(handle, ctypes.byref(nb), None, 0))
+    keys = None
+    if with_keys and nb.value > 0:
+        keys = np.zeros((nb.value, 3), np.int32)
+        st = int(lib().cvx_block_hash_info(handle, ctypes.byref(nb), keys.ctypes.data_as(ctypes.c_void_p),
+                                           nb.value))
+    return st, int(nb.value), keys
+
+
+def cvx_block_hash_destroy(handle: int) -> None:
+    lib().cvx_block_hash_destroy(handle)
 
 
 def cvx_flush_submap(handle: int, stream=None) -> None:

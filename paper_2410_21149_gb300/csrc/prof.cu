@@ -13,7 +13,8 @@ const char* kNames[covox::kNumKinds] = {"alloc_kernel",    "integrate_kernel", "
                                         "zero_pool_kernel", "batched_kernel", "features_kernel",
                                         "mlp_fwd_kernel",  "mlp_bwd_kernel", "adam_kernel",
                                         "targets_kernel", "integrate_pipelined_kernel", "flush_kernel",
-                                        "pipe_close_kernel", "esdf_kernels"};
+                                        "pipe_close_kernel", "esdf_kernels",
+                                        "hash_kernels"};
 
 struct Rec {
   int kind;

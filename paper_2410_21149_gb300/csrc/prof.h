@@ -22,7 +22,8 @@ enum KernelKind : int {
   kKFlush = 11,     // merge of a pipelined submap's pending scan
   kKPipeClose = 12, // pipelined per-scan bookkeeping after each scan
   kKEsdf = 13,      // distance field of a submap
-  kNumKinds = 14
+  kKHash = 14,      // stand-alone block hash insert / find
+  kNumKinds = 15
 };
 
 void prof_begin(int kind, cudaStream_t s);
