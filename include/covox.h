@@ -185,6 +185,23 @@ cvx_status cvx_submap_counters(cvx_submap* map, cvx_counters* out);
 cvx_status cvx_compute_esdf(cvx_submap* map, float site_band, float w_min, float max_dist, float* out,
                             int32_t* sq_dist, void* stream);
 
+/* Registration points (Sec. III-F: the backend's ICP takes each submap's
+ * points by their weights; the selection rule is the library's reading): the
+ * centres, in the submap frame (metres, ((i + 1/2) * voxel_size) in FP32),
+ * of the allocated voxels with W >= w_min, W > 0 and |D| <= d_band, in no
+ * particular order.  xyz: device float32 [capacity,3]; *n_out receives the
+ * number of qualifying voxels, of which the first min(*n_out, capacity) are
+ * written.  A pipelined submap's pending scan is merged first.  Synchronises
+ * `stream`. */
+cvx_status cvx_registration_points(cvx_submap* map, float w_min, float d_band, int64_t capacity, float* xyz,
+                                   int64_t* n_out, void* stream);
+
+/* Axis-aligned bounds of the allocated blocks in the submap frame, for the
+ * backend's overlap test (Sec. III-F): lo_hi = {lo x, y, z, hi x, y, z}
+ * (block corners, metres, FP32); lo > hi when the submap is empty.
+ * Synchronises `stream`. */
+cvx_status cvx_submap_bounds(cvx_submap* map, float lo_hi[6], void* stream);
+
 /* Free the submap and everything it allocated (synchronises its stream). */
 void cvx_destroy(cvx_submap* map);
 

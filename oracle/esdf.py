@@ -1,5 +1,6 @@
-"""Oracle of the submap ESDF -- TEST INFRASTRUCTURE ONLY (tests, smoke and the
-benchmark's CPU leg).
+"""Oracle of the submap ESDF and of the backend's submap queries (registration
+points, bounds) -- TEST INFRASTRUCTURE ONLY (tests, smoke and the benchmark's
+CPU leg).
 
 coVoxSLAM computes a Euclidean signed-distance field from the TSDF blocks
 (Sec. III-E, following the Parallel Banding Algorithm); the paper does not
@@ -109,3 +110,24 @@ def esdf(keys, D, W, vs, site_band, w_min, max_dist) -> np.ndarray:
     d2 = grid[rel[:, 0], rel[:, 1], rel[:, 2]].astype(np.float64)
     out = np.where(d2 >= float(INF), float(max_dist), np.minimum(np.sqrt(d2) * vs, max_dist))
     return out.reshape(len(keys), 512)
+
+
+def registration_points(keys, D, W, vs, w_min, d_band) -> np.ndarray:
+    """Centres (submap frame, metres, ((i + 1/2) * vs) rounded to FP32) of the
+    allocated voxels with W >= w_min, W > 0 and |D| <= d_band -- the points the
+    backend's registration takes from a submap by their weights (Sec. III-F;
+    the selection rule is this project's reading).  Rows sorted."""
+    keys = np.asarray(keys)
+    D = np.asarray(D, np.float32)
+    W = np.asarray(W, np.float32)
+    take = (W >= np.float32(w_min)) & (W > 0) & (np.abs(D) <= np.float32(d_band))
+    idx = _voxel_index(keys)[take].astype(np.float32)
+    c = (idx + np.float32(0.5)) * np.float32(vs)
+    return c[np.lexsort((c[:, 2], c[:, 1], c[:, 0]))] if len(c) else c.reshape(0, 3)
+
+
+def submap_bounds(keys, vs) -> np.ndarray:
+    """Block-corner box of the allocated blocks: lo xyz, hi xyz (FP32 metres)."""
+    keys = np.asarray(keys).astype(np.float32)
+    bs = np.float32(8) * np.float32(vs)
+    return np.concatenate([keys.min(0) * bs, (keys.max(0) + 1) * bs]).astype(np.float32)

@@ -91,6 +91,8 @@ SIGNATURES = {
     "cvx_reset_submap": (_i32, [_vp, _vp]),
     "cvx_submap_status": (_i32, [_vp]),
     "cvx_flush_submap": (_i32, [_vp, _vp]),
+    "cvx_registration_points": (_i32, [_vp, ctypes.c_float, ctypes.c_float, _i64, _vp, _vp, _vp]),
+    "cvx_submap_bounds": (_i32, [_vp, _vp, _vp]),
     "cvx_block_hash_create": (_i32, [_i64, _i64, _vp]),
     "cvx_block_hash_insert": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "cvx_block_hash_find": (_i32, [_vp, _vp, _i64, _vp, _vp]),
@@ -262,6 +264,24 @@ def cvx_compute_esdf(handle: int, site_band: float, w_min: float, max_dist: floa
     q = _dev_ptr(sq_dist, "torch.int32", "sq_dist") if sq_dist is not None else None
     check(lib().cvx_compute_esdf(handle, float(site_band), float(w_min), float(max_dist), o, q,
                                  _stream_handle(stream)), "cvx_compute_esdf")
+
+
+def cvx_registration_points(handle: int, w_min: float, d_band: float, xyz=None, stream=None) -> int:
+    """Writes into xyz (float32 CUDA tensor [capacity,3]) if given; returns the
+    number of qualifying voxels (synchronous)."""
+    n = ctypes.c_int64(0)
+    cap = int(xyz.shape[0]) if xyz is not None else 0
+    ptr = _dev_ptr(xyz, "torch.float32", "xyz") if cap else None
+    check(lib().cvx_registration_points(handle, float(w_min), float(d_band), cap, ptr, ctypes.byref(n),
+                                        _stream_handle(stream)), "cvx_registration_points")
+    return int(n.value)
+
+
+def cvx_submap_bounds(handle: int, stream=None) -> np.ndarray:
+    out = np.zeros(6, np.float32)
+    check(lib().cvx_submap_bounds(handle, out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)),
+          "cvx_submap_bounds")
+    return out
 
 
 def cvx_block_hash_create(slots: int, max_blocks: int) -> int:

@@ -1,4 +1,5 @@
-// esdf.cu -- Euclidean distance field of a submap (coVoxSLAM Sec. III-E).
+// esdf.cu -- Euclidean distance field of a submap (coVoxSLAM Sec. III-E),
+// and the submap queries of the backend (registration points, bounds).
 //
 // For every voxel of every allocated block: the distance between its centre
 // and the centre of the nearest site voxel (W > w_min and |D| <= site_band),
@@ -273,4 +274,125 @@ extern "C" cvx_status cvx_compute_esdf(cvx_submap* map, float site_band, float w
   const bool launched = cudaGetLastError() == cudaSuccess;
   scratch_free(map, mem, grid_bytes + scr_bytes, s);
   return launched ? CVX_OK : CVX_ERR_CUDA;
+}
+
+// ------------------------------------------------ registration points, bounds
+// The backend's ICP takes its points from each submap by their weights and
+// finds overlapping submaps by axis-aligned boxes (Sec. III-F).  Library
+// reading: the registration points are the centres of the allocated voxels
+// with W >= w_min and |D| <= d_band, compacted with one atomic per warp.
+namespace {
+
+__global__ void regpoints_kernel(SubmapDev m, int nb, float w_min, float d_band, long long capacity,
+                                 float* __restrict__ xyz, unsigned long long* __restrict__ count) {
+  const int lane = threadIdx.x & 31;
+  const size_t total = (size_t)nb * kVoxPerBlock;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e0 = (size_t)blockIdx.x * blockDim.x; e0 < total; e0 += stride) {   // warp-uniform
+    const size_t e = e0 + threadIdx.x;
+    bool take = false;
+    if (e < total) {
+      float D, W;
+      if (m.storage == CVX_STORE_F32) {
+        D = ((const float*)m.D)[e];
+        W = ((const float*)m.W)[e];
+      } else {
+        D = __half2float(((const __half*)m.D)[e]) * m.trunc;
+        W = __half2float(((const __half*)m.W)[e]);
+      }
+      take = W >= w_min && W > 0.0f && fabsf(D) <= d_band;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    unsigned long long base = 0;
+    if (lane == 0 && bal) base = atomicAdd(count, (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (take) {
+      const unsigned long long at = base + __popc(bal & ((1u << lane) - 1u));
+      if ((long long)at < capacity) {
+        const int b = (int)(e / kVoxPerBlock), l = (int)(e % kVoxPerBlock);
+        const int v0 = m.block_keys[3 * b] * 8 + (l & 7);
+        const int v1 = m.block_keys[3 * b + 1] * 8 + ((l >> 3) & 7);
+        const int v2 = m.block_keys[3 * b + 2] * 8 + (l >> 6);
+        xyz[3 * at] = __fmul_rn((float)v0 + 0.5f, m.vs);
+        xyz[3 * at + 1] = __fmul_rn((float)v1 + 0.5f, m.vs);
+        xyz[3 * at + 2] = __fmul_rn((float)v2 + 0.5f, m.vs);
+      }
+    }
+  }
+}
+
+// the submap's block count (synchronous); -1 on a CUDA error
+int read_blocks(cvx_submap* map, cudaStream_t s) {
+  int32_t nb32 = 0;
+  if (cudaMemcpyAsync(&nb32, &map->dev.st->n_blocks, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return std::min<int32_t>(nb32, map->dev.max_blocks);
+}
+
+}  // namespace
+
+extern "C" cvx_status cvx_registration_points(cvx_submap* map, float w_min, float d_band, int64_t capacity,
+                                              float* xyz, int64_t* n_out, void* stream) {
+  if (!map || !n_out || capacity < 0 || (capacity > 0 && !xyz) || !(d_band >= 0) || !std::isfinite(d_band) ||
+      !std::isfinite(w_min))
+    return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  map->last_stream = s;
+  if (flush_pending(map, s, false) != CVX_OK) return CVX_ERR_CUDA;
+  const int nb = read_blocks(map, s);
+  if (nb < 0) return CVX_ERR_CUDA;
+  *n_out = 0;
+  if (nb == 0) return CVX_OK;
+  unsigned long long* count = (unsigned long long*)scratch_alloc(map, 64, s);
+  if (!count) return CVX_ERR_OOM;
+  unsigned long long h = 0;
+  cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+  COVOX_LAUNCH(kKEsdf, s, regpoints_kernel<<<num_sms() * 8, 256, 0, s>>>(map->dev, nb, w_min, d_band, capacity,
+                                                                         xyz, count));
+  const bool ok = cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                  cudaStreamSynchronize(s) == cudaSuccess;
+  scratch_free(map, count, 64, s);
+  if (!ok) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  *n_out = (int64_t)h;
+  return CVX_OK;
+}
+
+extern "C" cvx_status cvx_submap_bounds(cvx_submap* map, float lo_hi[6], void* stream) {
+  if (!map || !lo_hi) return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  map->last_stream = s;
+  const int nb = read_blocks(map, s);
+  if (nb < 0) return CVX_ERR_CUDA;
+  if (nb == 0) {
+    for (int c = 0; c < 3; ++c) {
+      lo_hi[c] = 1.0f;
+      lo_hi[3 + c] = 0.0f;
+    }
+    return CVX_OK;
+  }
+  int* box = (int*)scratch_alloc(map, 64, s);
+  if (!box) return CVX_ERR_OOM;
+  int hb[6];
+  COVOX_LAUNCH(kKEsdf, s, esdf_box_init_kernel<<<1, 32, 0, s>>>(box));
+  COVOX_LAUNCH(kKEsdf, s, esdf_bbox_kernel<<<std::min(num_sms() * 4, (nb + 255) / 256), 256, 0, s>>>(
+                              map->dev.block_keys, nb, box));
+  const bool ok = cudaMemcpyAsync(hb, box, sizeof(hb), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                  cudaStreamSynchronize(s) == cudaSuccess;
+  scratch_free(map, box, 64, s);
+  if (!ok) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  const float bs = 8.0f * map->p.voxel_size;
+  for (int c = 0; c < 3; ++c) {
+    lo_hi[c] = (float)hb[c] * bs;
+    lo_hi[3 + c] = (float)(hb[3 + c] + 1) * bs;
+  }
+  return CVX_OK;
 }

@@ -98,3 +98,17 @@ def test_no_sites_gives_cap():
     D = np.ones((2, 512))
     W = np.ones((2, 512))
     assert (oe.esdf(keys, D, W, VS, 0.05, 0.0, 0.7) == 0.7).all()
+
+
+def test_registration_points_and_bounds_by_hand():
+    keys = np.array([[0, 0, 0], [-1, 2, 0]], np.int32)
+    D = np.full((2, 512), 0.5)
+    W = np.zeros((2, 512))
+    D[0, 0], W[0, 0] = 0.01, 2.0          # voxel (0,0,0): taken
+    D[0, 9], W[0, 9] = -0.02, 0.5         # voxel (1,1,0): W below w_min
+    D[1, 64 + 7], W[1, 64 + 7] = 0.0, 1.0  # voxel (-8+7, 16, 1) = (-1, 16, 1): taken
+    D[1, 3], W[1, 3] = 0.2, 5.0           # |D| above the band
+    pts = oe.registration_points(keys, D, W, 0.1, 1.0, 0.05)
+    want = np.array([[-0.05, 1.65, 0.15], [0.05, 0.05, 0.05]], np.float32)
+    assert np.allclose(pts, want, rtol=0, atol=1e-7)
+    assert np.allclose(oe.submap_bounds(keys, 0.1), [-0.8, 0.0, 0.0, 0.8, 2.4, 0.8], atol=1e-6)

@@ -96,3 +96,25 @@ def test_no_sites_and_empty_submap():
     with pytest.raises(cvx.CovoxError):
         sub.esdf(max_dist=0.0)
     sub.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_registration_points_and_bounds(storage):
+    import torch
+    from oracle import esdf as oe
+    from paper_2410_21149_gb300 import _capi
+    wl = sg.make_c1(n_frames=3)
+    sub = _integrate(wl, storage)
+    keys, D, W = _oracle_inputs(sub)
+    w_min, band = 1.5, 0.05
+    n = _capi.cvx_registration_points(sub.handle, w_min, band)          # count only
+    xyz = torch.empty((n + 7, 3), dtype=torch.float32, device="cuda")
+    assert _capi.cvx_registration_points(sub.handle, w_min, band, xyz) == n
+    got = xyz[:n].cpu().numpy()
+    got = got[np.lexsort((got[:, 2], got[:, 1], got[:, 0]))]
+    want = oe.registration_points(keys, D, W, np.float32(sub.voxel_size), w_min, band)
+    assert n > 100 and np.array_equal(got, want)
+    small = torch.empty((10, 3), dtype=torch.float32, device="cuda")
+    assert _capi.cvx_registration_points(sub.handle, w_min, band, small) == n   # count beyond capacity
+    assert np.array_equal(_capi.cvx_submap_bounds(sub.handle), oe.submap_bounds(keys, np.float32(sub.voxel_size)))
+    sub.close()
