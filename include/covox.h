@@ -108,8 +108,15 @@ typedef struct {
                             32-pixel-wide tiles of pts_per_cta / 32 rows) */
   int32_t local_blocks;  /* tuning: shared-memory block slots per CTA: 0 = default (8), a
                             power of two <= 16, or -1 = no shared slots (global atomics) */
-  int32_t reserved;      /* must be 0 */
+  int32_t flags;         /* 0, or CVX_INTEGRATE_CARVE */
 } cvx_integrate_params;
+
+/* Free-space carving (the paper's ray casting from the optical centre,
+ * Sec. III-C): each ray is traversed from the sensor origin to
+ * p + trunc u instead of over the band [p - trunc u, p + trunc u]; voxels in
+ * front of the band receive d = +trunc.  A = origin / voxel_size replaces
+ * (p - trunc u) / voxel_size in the traversal; everything else is unchanged. */
+#define CVX_INTEGRATE_CARVE 1
 
 typedef struct {
   int64_t n_blocks;         /* allocated blocks */

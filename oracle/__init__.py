@@ -54,7 +54,7 @@ def lib():
             L.orc_point_obs.argtypes = [vp, vp, f32, f32, f32, f32, i32, i32, i32, f32, vp, vp, vp,
                                         i32, vp]
             L.orc_integrate.restype = i32
-            L.orc_integrate.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp]
+            L.orc_integrate.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp, i32]
             L.orc_extract.argtypes = [vp, vp, vp, vp]
             L.orc_block_set.restype = i64
             L.orc_block_set.argtypes = [vp, vp, vp, i32, f32, f32, f32, f32, vp, vp, i64]
@@ -87,14 +87,15 @@ class OracleSubmap:
 
     def integrate(self, points: np.ndarray, T: np.ndarray, point_weights: Optional[np.ndarray] = None,
                   weight_mode: int = 0, dropoff: int = 0, min_range: float = 0.1,
-                  max_range: float = 1e9, sensor: int = 0) -> Dict[str, int]:
-        """One frame; returns the frame's counts and status (0 or -4 key range)."""
+                  max_range: float = 1e9, sensor: int = 0, carve: bool = False) -> Dict[str, int]:
+        """One frame; returns the frame's counts and status (0 or -4 key range).
+        carve: traverse from the sensor origin (free-space carving)."""
         pts = _f32(points).reshape(-1, 3)
         Tm = _f32(T).reshape(12)
         pw = None if point_weights is None else _f32(point_weights)
         stats = np.zeros(6, dtype=np.int64)
         rc = lib().orc_integrate(self.h, _p(pts), len(pts), _p(Tm), _p(pw), weight_mode, dropoff,
-                                 min_range, max_range, sensor, _p(stats))
+                                 min_range, max_range, sensor, _p(stats), 1 if carve else 0)
         keys = ("valid", "obs", "voxels", "blocks", "new_blocks", "key_range")
         out = dict(zip(keys, (int(x) for x in stats)))
         out["status"] = rc

@@ -9,7 +9,8 @@
  *   - every valid point of a scan is used (Sec. III-C, raycasting paragraph);
  *   - each point's ray is traversed over the band [-trunc, +trunc] around the
  *     point (raycasting from the optical centre, restricted to the truncation
- *     band), voxel by voxel with an Amanatides-Woo traversal;
+ *     band), voxel by voxel with an Amanatides-Woo traversal; with carving,
+ *     from the optical centre itself to trunc behind the point;
  *   - the voxels are grouped in 8^3 blocks indexed by their integer 3-D
  *     position (Sec. III-C, "indexed by their 3D position");
  *   - per scan, the weighted distances of all observations of a voxel are
@@ -139,13 +140,15 @@ int traverse(const float* A, const float* B, std::vector<Key>* out) {
   return n + 1;
 }
 
-// Band endpoints a = p - trunc u, b = p + trunc u, scaled by 1/vs.
+// Band endpoints a = p - trunc u, b = p + trunc u, scaled by 1/vs.  With
+// free-space carving the segment starts at the sensor origin instead
+// (a = o: the ray cast from the optical centre, Sec. III-C).
 // Returns false if either endpoint leaves the +-2^23 voxel key range.
-bool band_segment(const Ray& ray, float trunc, float vs, float* A, float* B) {
+bool band_segment(const Ray& ray, float trunc, float vs, float* A, float* B, bool carve = false) {
   float inv_vs = 1.0f / vs;
   for (int k = 0; k < 3; ++k) {
     float tu = trunc * ray.u[k];
-    float a = ray.p[k] - tu;
+    float a = carve ? ray.o[k] : ray.p[k] - tu;
     float b = ray.p[k] + tu;
     A[k] = a * inv_vs;
     B[k] = b * inv_vs;
@@ -300,7 +303,7 @@ int orc_point_obs(const float* ps, const float* T, float vs, float trunc, float 
  * merge of that frame is skipped while newly seen blocks stay allocated). */
 int orc_integrate(void* h, const float* pts, int64_t n, const float* T, const float* pw,
                   int weight_mode, int dropoff, float min_range, float max_range, int sensor,
-                  int64_t* stats) {
+                  int64_t* stats, int carve) {
   Map* m = (Map*)h;
   // Frame sums keyed by voxel, accumulated in point-index order.
   std::map<Key, std::pair<double, double>> frame;
@@ -311,7 +314,7 @@ int orc_integrate(void* h, const float* pts, int64_t n, const float* T, const fl
     Ray ray;
     if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) continue;
     float A[3], B[3];
-    if (!band_segment(ray, m->trunc, m->vs, A, B)) {
+    if (!band_segment(ray, m->trunc, m->vs, A, B, carve != 0)) {
       ++bad;
       continue;
     }

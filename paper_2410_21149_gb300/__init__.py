@@ -41,10 +41,10 @@ def _torch_allocator():
 
 def integrate_params(weight_mode=CVX_W_CONST, dropoff=CVX_DROP_NONE, min_range=0.1,
                      max_range=1e9, sensor=CVX_SENSOR_PINHOLE, height=0, width=0,
-                     pts_per_cta=0, local_blocks=0) -> cvx_integrate_params:
+                     pts_per_cta=0, local_blocks=0, carve=False) -> cvx_integrate_params:
     return cvx_integrate_params(int(weight_mode), int(dropoff), float(min_range), float(max_range),
                                 int(height), int(width), int(sensor), int(pts_per_cta),
-                                int(local_blocks), 0)
+                                int(local_blocks), _capi.CVX_INTEGRATE_CARVE if carve else 0)
 
 
 class Submap:

@@ -24,6 +24,7 @@ CVX_W_CONST, CVX_W_QUADRATIC, CVX_W_PER_POINT = 0, 1, 2
 CVX_DROP_NONE, CVX_DROP_LINEAR, CVX_DROP_QUADRATIC = 0, 1, 2
 CVX_SENSOR_PINHOLE, CVX_SENSOR_SPHERICAL = 0, 1
 CVX_SUBMAP_PIPELINED = 1
+CVX_INTEGRATE_CARVE = 1
 
 STATUS_NAMES = {0: "CVX_OK", -1: "CVX_ERR_INVALID_ARG", -2: "CVX_ERR_OOM", -3: "CVX_ERR_CAPACITY",
                 -4: "CVX_ERR_KEY_RANGE", -5: "CVX_ERR_TIMEOUT", -6: "CVX_ERR_CUDA"}
@@ -52,7 +53,7 @@ class cvx_integrate_params(ctypes.Structure):
                 ("min_range", ctypes.c_float), ("max_range", ctypes.c_float),
                 ("height", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("sensor", ctypes.c_int32), ("pts_per_cta", ctypes.c_int32),
-                ("local_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("local_blocks", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class cvx_counters(ctypes.Structure):

@@ -525,7 +525,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   // one variant for every scan: a kernel holding only that code
   int variant = -2;
   for (int k = 0; k < n_run; ++k) {
-    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff);
+    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff, sd[order[k]].carve);
     variant = variant == -2 ? v : (variant == v ? v : -1);
   }
   const BatchedFn kern = kBatched[variant + 1];

@@ -40,7 +40,7 @@ struct SubmapDev {
   int32_t* block_keys;        // [max_blocks,3] integer block coordinates
   void* D;                    // [max_blocks,512] float or half (D / trunc)
   void* W;                    // [max_blocks,512] float or half
-  float2* acc;                // [max_blocks,512] per-scan sums (sum w d, sum w), zero between scans
+  float2* acc;                // [max_blocks,512] per-scan sums (sum w (d - trunc), sum w), zero between scans
   int32_t* touched;           // [max_blocks] pool index of each block touched by the scan
   State* st;
   int32_t* n_touched;         // per-scan counters of this view (&st->n_touched or _b)
@@ -63,6 +63,7 @@ struct ScanDev {
   float T[12];           // submap <- sensor, row-major 3x4
   float min_range, max_range;
   int32_t weight_mode, dropoff, sensor, organised;
+  int32_t carve;         // traverse from the sensor origin (free-space carving)
   int32_t height, width, tile_w, tile_h, tiles_x, n_tiles;
 };
 
@@ -128,14 +129,16 @@ __device__ __forceinline__ bool make_ray(const ScanDev& sc, long long i, Ray& r)
 }
 
 // Band endpoints in voxel units: A = (p - trunc u) / vs, B = (p + trunc u) / vs
-// (the division is a multiply by the FP32 reciprocal of vs).  False if an
-// endpoint leaves the key range.
-__device__ __forceinline__ bool band(const Ray& r, float trunc, float inv_vs, float A[3], float B[3]) {
+// (the division is a multiply by the FP32 reciprocal of vs); with carving,
+// A = o / vs (the ray starts at the sensor origin).  False if an endpoint
+// leaves the key range.
+__device__ __forceinline__ bool band(const Ray& r, float trunc, float inv_vs, float A[3], float B[3],
+                                     bool carve = false) {
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const float tu = __fmul_rn(trunc, r.u[k]);
-    A[k] = __fmul_rn(__fsub_rn(r.p[k], tu), inv_vs);
+    A[k] = carve ? __fmul_rn(r.o[k], inv_vs) : __fmul_rn(__fsub_rn(r.p[k], tu), inv_vs);
     B[k] = __fmul_rn(__fadd_rn(r.p[k], tu), inv_vs);
     ok = ok && (A[k] >= -kKeyLimit) && (A[k] < kKeyLimit) && (B[k] >= -kKeyLimit) && (B[k] < kKeyLimit);
   }

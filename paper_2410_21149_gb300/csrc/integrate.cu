@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(kTileThreads) integrate_kernel(SubmapDev m, Sc
 }
 
 using IntegrateFn = void (*)(SubmapDev, ScanDev, int);
-const IntegrateFn kIntegrate[6] = {integrate_kernel<0>, integrate_kernel<1>, integrate_kernel<2>,
-                                   integrate_kernel<3>, integrate_kernel<4>, integrate_kernel<5>};
+const IntegrateFn kIntegrate[7] = {integrate_kernel<-1>, integrate_kernel<0>, integrate_kernel<1>,
+                                   integrate_kernel<2>,  integrate_kernel<3>, integrate_kernel<4>,
+                                   integrate_kernel<5>};   // [variant + 1]
 
 template <int kStore>
 __global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
@@ -245,9 +246,10 @@ __global__ void pipe_close_kernel(SubmapDev a, SubmapDev b) {
 }
 
 using PipelinedFn = void (*)(SubmapDev, SubmapDev, ScanDev, int, int);
-const PipelinedFn kPipelined[6] = {integrate_pipelined_kernel<0>, integrate_pipelined_kernel<1>,
-                                   integrate_pipelined_kernel<2>, integrate_pipelined_kernel<3>,
-                                   integrate_pipelined_kernel<4>, integrate_pipelined_kernel<5>};
+const PipelinedFn kPipelined[7] = {integrate_pipelined_kernel<-1>, integrate_pipelined_kernel<0>,
+                                   integrate_pipelined_kernel<1>,  integrate_pipelined_kernel<2>,
+                                   integrate_pipelined_kernel<3>,  integrate_pipelined_kernel<4>,
+                                   integrate_pipelined_kernel<5>};   // [variant + 1]
 
 // Merge the pending scan of a pipelined submap (no-op when none is pending).
 // discard: clear its sums without touching D and W.
@@ -410,7 +412,7 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
   const size_t smem = tile_smem_bytes(lb);
   static bool attr_set = false;
   if (!attr_set) {
-    for (int v = 0; v < 6; ++v)
+    for (int v = 0; v < 7; ++v)
       cudaFuncSetAttribute((const void*)kIntegrate[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tile_smem_bytes(kMaxLocalBlocks));
     attr_set = true;
@@ -418,13 +420,13 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
   if (map->pipelined) {
     static bool pattr_set = false;
     if (!pattr_set) {
-      for (int v = 0; v < 6; ++v)
+      for (int v = 0; v < 7; ++v)
         cudaFuncSetAttribute((const void*)kPipelined[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tile_smem_bytes(kMaxLocalBlocks));
       pattr_set = true;
     }
     const int n_merge = num_sms();
-    const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff)];
+    const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff, sc.carve) + 1];
     COVOX_LAUNCH(kKPipelined, s,
                  pf<<<n_merge + sc.n_tiles, kTileThreads, smem, s>>>(map->dev, map->dev_b, sc, lb, n_merge));
     COVOX_LAUNCH(kKPipeClose, s, pipe_close_kernel<<<1, 1, 0, s>>>(map->dev, map->dev_b));
@@ -432,7 +434,7 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
     map->maybe_pending = true;
     return CVX_OK;
   }
-  const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff)];
+  const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff, sc.carve) + 1];
   COVOX_LAUNCH(kKAccum, s, fn<<<sc.n_tiles, kTileThreads, smem, s>>>(map->dev, sc, lb));
   const int grid = std::min<int>(map->dev.max_blocks, num_sms() * 2);
   if (map->p.storage == CVX_STORE_F32)

@@ -180,6 +180,11 @@ constexpr int kCache = 256;         // block -> pool cache entries per CTA (powe
 constexpr int kCachePending = -2;
 constexpr int kCacheWait = 4096;    // polls of a pending cache entry before activating anyway
 
+// The per-scan sums of a voxel are (sum w (d - trunc), sum w): distances are
+// summed relative to +trunc, so the many observations of free space (d
+// clamped to +trunc) add exact zeros, and D is recovered as
+// trunc + ((D - trunc) W + sum w (d - trunc)) / (W + sum w) -- the same value
+// as (D W + sum w d) / (W + sum w).
 // Shared per-voxel sums are exact 64-bit fixed point X = hi * 2^S + lo held
 // in two 32-bit words (lo unsigned, < 2^S per observation; hi signed), so
 // every update is two native 32-bit integer atomics, which the hardware
@@ -313,7 +318,7 @@ __device__ __forceinline__ int local_slot(const TileSmem& t, int lb, unsigned lo
   return -1;
 }
 
-template <bool kLocal, int kDrop>
+template <bool kLocal, int kDrop, bool kCarve = false>
 __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
   const TileSmem t = tile_smem(smem, lb);
   const int tid = threadIdx.x;
@@ -369,7 +374,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     Ray r;
     if (!make_ray(sc, i, r)) continue;
     float A[3], B[3];
-    if (!band(r, m.trunc, m.inv_vs, A, B)) {
+    if (!band(r, m.trunc, m.inv_vs, A, B, kCarve)) {
       atomicOr(m.frame_err, kErrKeyRange);
       continue;
     }
@@ -406,10 +411,10 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
       }
       if (kLocal && slot >= 0) {
         const int e = slot * kVoxPerBlock + l;
-        fixed_add(t.lo_wd + e, t.hi_wd + e, fx.S, __float2ll_rn(w * dc * fx.scale));
+        fixed_add(t.lo_wd + e, t.hi_wd + e, fx.S, __float2ll_rn(w * (dc - m.trunc) * fx.scale));
         fixed_add(t.lo_w + e, t.hi_w + e, fx.S, __float2ll_rn(w * fx.scale));
       } else if (gpool >= 0) {
-        red_add2(m.acc + (size_t)gpool * kVoxPerBlock + l, w * dc, w);
+        red_add2(m.acc + (size_t)gpool * kVoxPerBlock + l, w * (dc - m.trunc), w);
       }
       if (d.left == 0) break;
       // next axis: the traversal rule of Dda::step, as selects
@@ -427,6 +432,10 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
       } else {
         sk = d.s[2]; d.v[2] += sk; d.tm[2] = __fadd_rn(d.tm[2], d.td[2]); dist += dd2; stride = 64; shift = 0;
       }
+      // A carved ray reaches the band after many steps of free space, where
+      // the clamp hides the drift of the running sum; near the band the
+      // distance is recomputed exactly.
+      if (kCarve && dist < m.trunc + 2.0f * m.vs) dist = voxel_distance_raw(r, d.v, m.vs);
       const int mask = 7 * stride;
       const int f = ((l & mask) + sk * stride) & mask;
       l = (l & ~mask) | f;
@@ -490,21 +499,32 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
 // tile; lb == 0: every observation is a vector atomic on the block's global
 // per-scan sums (the L2 performs the float additions).  The accumulation and
 // drop-off modes are compile-time variants.
-__device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+template <bool kCarve>
+__device__ inline void integrate_tile_c(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
   if (lb > 0) {
-    if (sc.dropoff == 0) integrate_tile_t<true, 0>(m, sc, tile, smem, lb);
-    else if (sc.dropoff == 1) integrate_tile_t<true, 1>(m, sc, tile, smem, lb);
-    else integrate_tile_t<true, 2>(m, sc, tile, smem, lb);
+    if (sc.dropoff == 0) integrate_tile_t<true, 0, kCarve>(m, sc, tile, smem, lb);
+    else if (sc.dropoff == 1) integrate_tile_t<true, 1, kCarve>(m, sc, tile, smem, lb);
+    else integrate_tile_t<true, 2, kCarve>(m, sc, tile, smem, lb);
   } else {
-    if (sc.dropoff == 0) integrate_tile_t<false, 0>(m, sc, tile, smem, lb);
-    else if (sc.dropoff == 1) integrate_tile_t<false, 1>(m, sc, tile, smem, lb);
-    else integrate_tile_t<false, 2>(m, sc, tile, smem, lb);
+    if (sc.dropoff == 0) integrate_tile_t<false, 0, kCarve>(m, sc, tile, smem, lb);
+    else if (sc.dropoff == 1) integrate_tile_t<false, 1, kCarve>(m, sc, tile, smem, lb);
+    else integrate_tile_t<false, 2, kCarve>(m, sc, tile, smem, lb);
   }
+}
+
+// Any scan: accumulation mode, drop-off and carving chosen at run time
+// (carved rays keep the ray for exact distances near the band, which costs
+// registers the plain variants need not hold).
+__device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+  if (sc.carve) integrate_tile_c<true>(m, sc, tile, smem, lb);
+  else integrate_tile_c<false>(m, sc, tile, smem, lb);
 }
 
 // Variant index of a scan: accumulation mode x drop-off (0..5), so a launch
 // whose scans share one variant runs a kernel holding only that code.
-__host__ __device__ inline int tile_variant(int lb, int dropoff) { return (lb > 0 ? 3 : 0) + dropoff; }
+__host__ __device__ inline int tile_variant(int lb, int dropoff, int carve) {
+  return carve ? -1 : (lb > 0 ? 3 : 0) + dropoff;   // -1: the run-time dispatching kernel
+}
 
 template <int kVariant>
 __device__ __forceinline__ void integrate_tile_v(const SubmapDev& m, const ScanDev& sc, int tile, char* smem,
@@ -596,7 +616,7 @@ __device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, b
       for (int q = 0; q < 4; ++q)
         if (wa[q] != 0.0f) {
           const float wn = Wa[q] + wa[q];
-          Da[q] = (Da[q] * Wa[q] + swa[q]) / wn;
+          Da[q] = m.trunc + ((Da[q] - m.trunc) * Wa[q] + swa[q]) / wn;
           Wa[q] = fminf(wn, m.max_w);
           ++merged;
         }
@@ -611,7 +631,7 @@ __device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, b
       for (int q = 0; q < 4; ++q)
         if (wb[q] != 0.0f) {
           const float wn = Wb[q] + wb[q];
-          Db[q] = (Db[q] * Wb[q] + swb[q]) / wn;
+          Db[q] = m.trunc + ((Db[q] - m.trunc) * Wb[q] + swb[q]) / wn;
           Wb[q] = fminf(wn, m.max_w);
           ++merged;
         }

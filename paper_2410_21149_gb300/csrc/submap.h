@@ -65,6 +65,7 @@ inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t
       (ip->local_blocks > 0 && (ip->local_blocks & (ip->local_blocks - 1)) != 0))
     return CVX_ERR_INVALID_ARG;   // -1, 0 or a power of two
   if (ip->height < 0 || ip->width < 0) return CVX_ERR_INVALID_ARG;
+  if (ip->flags & ~CVX_INTEGRATE_CARVE) return CVX_ERR_INVALID_ARG;
   if (n > (1ll << 31) - 1) return CVX_ERR_INVALID_ARG;
   std::memset(sc, 0, sizeof(*sc));
   sc->pts = pts;
@@ -76,6 +77,7 @@ inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t
   sc->weight_mode = ip->weight_mode;
   sc->dropoff = ip->dropoff;
   sc->sensor = ip->sensor;
+  sc->carve = (ip->flags & CVX_INTEGRATE_CARVE) ? 1 : 0;
   sc->organised = (ip->height > 0 && ip->width >= 32 && (int64_t)ip->height * ip->width == n) ? 1 : 0;
   sc->height = ip->height;
   sc->width = ip->width;

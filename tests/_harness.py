@@ -43,7 +43,7 @@ def run_gpu(wl: sg.Workload, storage=None, max_blocks=1 << 17, point_weights=Non
     return out
 
 
-def run_oracle(wl: sg.Workload, fp16=None, point_weights=None):
+def run_oracle(wl: sg.Workload, fp16=None, point_weights=None, carve=False):
     import oracle as orc
     fp16 = bool(wl.storage) if fp16 is None else fp16
     out = []
@@ -53,7 +53,7 @@ def run_oracle(wl: sg.Workload, fp16=None, point_weights=None):
         for k, sc in enumerate(sm.scans):
             pw = None if point_weights is None else point_weights[m][k]
             st = om.integrate(sc.points, sc.T_sub_sensor, pw, wl.weight_mode, wl.dropoff,
-                              wl.min_range, wl.max_range, sc.sensor)
+                              wl.min_range, wl.max_range, sc.sensor, carve=carve)
             for key, v in st.items():
                 tot[key] = tot.get(key, 0) + v
         keys, D, W = om.extract()

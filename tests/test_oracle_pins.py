@@ -424,3 +424,50 @@ def test_fp16_mode_stores_half_values():
     assert np.array_equal(Wh.astype(np.float16).astype(np.float64), Wh)
     # storage error vs the unrounded oracle stays within a few half ulps of trunc
     assert np.abs(Dh - Df).max() < 4 * 2.0 ** -11 * 0.3
+
+
+# ------------------------------------------------------ free-space carving
+def test_carving_axis_ray_closed_form():
+    """A ray along +x from the sensor at x = 0.05 to a point at x = 1.05
+    (vs 0.1, trunc 0.3): carving visits voxels 0..13 (floor((1.05 + 0.3) / 0.1)),
+    the band only 7..13; in front of the band d = +trunc, inside it
+    d = 1.05 - (i + 1/2) vs, clamped to +-trunc; weights 1."""
+    vs, tr = 0.1, 0.3
+    T = np.array([1, 0, 0, 0.05, 0, 1, 0, 0.05, 0, 0, 1, 0.05], np.float32)
+    p = np.array([[1.0, 0.0, 0.0]], np.float32)            # submap x = 1.05
+    out = {}
+    for carve in (False, True):
+        m = orc.OracleSubmap(vs, tr)
+        st = m.integrate(p, T, sensor=1, carve=carve)
+        keys, D, W = m.extract()
+        xs = [int(k[0]) * 8 + l for k, b in zip(keys, range(len(keys))) for l in range(8) if W[b, l] > 0]
+        out[carve] = (st, keys, D, W, sorted(xs))
+    assert out[False][4] == list(range(7, 14)) and out[True][4] == list(range(0, 14))
+    assert out[True][0]["obs"] == 14 and out[False][0]["obs"] == 7
+    keys, D, W = out[True][1], out[True][2], out[True][3]
+    for i in range(14):
+        b = [j for j, k in enumerate(keys.tolist()) if k == [i // 8, 0, 0]][0]
+        c = (np.float32(i) + 0.5) * np.float64(np.float32(vs))
+        want = min(max(float(np.float32(1.05)) - c, -tr), tr)
+        assert abs(D[b, i % 8] - want) < 1e-6 and W[b, i % 8] == 1.0
+
+
+def test_carving_extends_the_band():
+    """One ray: carving observes the band's voxels exactly as the band does and
+    adds the voxels from the sensor to the band, all at d = +trunc."""
+    rng = np.random.default_rng(7)
+    T = np.array([1, 0, 0, 0.3, 0, 1, 0, -0.2, 0, 0, 1, 0.1], np.float32)
+    for _ in range(5):
+        p = np.array([rng.uniform(-1, 1, 2).tolist() + [rng.uniform(1.5, 3.0)]], np.float32)
+        res = {}
+        for carve in (False, True):
+            m = orc.OracleSubmap(0.1, 0.3)
+            m.integrate(p, T, carve=carve)
+            keys, D, W = m.extract()
+            res[carve] = {(tuple(k), l): (D[b, l], W[b, l]) for b, k in enumerate(keys.tolist())
+                          for l in range(512) if W[b, l] > 0}
+        band, carved = res[False], res[True]
+        assert set(band) <= set(carved)
+        assert all(carved[k] == band[k] for k in band)
+        extra = [carved[k] for k in carved if k not in band]
+        assert extra and all(abs(d - 0.3) < 1e-6 and w == 1.0 for d, w in extra)
