@@ -552,8 +552,10 @@ def run_ours(args):
         "gpu_launches_per_step": launches_per_step,
         "clocks": clk,
     }
-    out["forms"]["esdf"] = esdf_form(sub32, stream, args, peaks)
-    out["forms"]["hash_stress"] = hash_stress_form(args)
+    if not args.no_extra:
+        out["forms"]["carving"] = carving_form(wl, pts, Ts, stream, args, ws, make_sub, capture, timed, prm_of)
+        out["forms"]["esdf"] = esdf_form(sub32, stream, args, peaks)
+        out["forms"]["hash_stress"] = hash_stress_form(args)
     if not args.no_learned:
         out["forms"]["learned_weight"] = learned_form(wl, pts, Ts, stream, args, ws, rmse32, ms32 / args.steps)
     if not args.no_batched:
@@ -578,6 +580,41 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def carving_form(wl, pts, Ts, stream, args, ws, make_sub, capture, timed, prm_of):
+    """Free-space carving on the multiroom frames: every ray traversed from the
+    optical centre to trunc behind its point (Sec. III-C), same launch shape,
+    FP32, CUDA-graph replay of whole steps like the headline."""
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    prm = prm_of(args.ppc, args.lb)
+    prm.flags = cvx._capi.CVX_INTEGRATE_CARVE
+    sub = make_sub(cvx.CVX_STORE_F32)
+    F = len(Ts)
+
+    def step_c():
+        sub.reset(stream)
+        for f in range(F):
+            sub.integrate(pts[f], Ts[f], prm, None, stream)
+        sub.flush(stream)
+
+    for _ in range(2):
+        step_c()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        step_c()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 5)
+    ms = max_over_ranks(timed(g, steps, args.warmup), ws) / steps
+    step_c()
+    torch.cuda.synchronize()
+    c = sub.counters()
+    assert sub.status() == 0
+    sub.close()
+    return {"points_per_s": c["valid_points"] / (ms / 1e3), "voxel_updates_per_s": c["observations"] / (ms / 1e3),
+            "ms_per_step": ms, "observations_per_step": c["observations"], "blocks_allocated": c["n_blocks"]}
 
 
 def esdf_form(sub, stream, args, peaks):
@@ -833,6 +870,8 @@ def main():
     ap.add_argument("--scans", type=int, default=2000, help="LiDAR scans (lidar workload)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched form (multiroom)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-weight form (multiroom)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the carving, ESDF and hash-stress forms (multiroom)")
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--ppc", type=int, default=0, help="points per CTA tile (0: autotuned)")
     ap.add_argument("--lb", type=int, default=0, help="shared block slots per CTA (-1: global atomics)")
