@@ -137,7 +137,8 @@ cvx_status cvx_create_submap(const cvx_submap_params* params, cvx_submap** out);
  * allocate, process).  points_xyz: device float32 [n,3], sensor frame, NaN or
  * out-of-range points skipped.  T_sub_sensor: HOST float32[12], 3x4 row-major
  * rigid transform submap <- sensor (its translation is the sensor origin).
- * point_weights: device float32 [n] for CVX_W_PER_POINT, else NULL.
+ * point_weights: device float32 [n] for CVX_W_PER_POINT, else NULL; a point
+ * whose weight is not finite or is negative is invalid (skipped, not counted).
  * For every valid point p with unit ray direction u from the origin o, each
  * voxel v crossed by the segment [p - trunc u, p + trunc u] receives the
  * observation d = clamp((p - c_v).u, -trunc, trunc) (c_v = voxel centre) with
@@ -368,8 +369,13 @@ cvx_status cvx_training_targets(cvx_submap* clean, const float* points_xyz, int6
  *     give CVX_ERR_INVALID_ARG.  Device errors behave as in
  *     cvx_integrate_scan() and are recorded in the view's state buffer.
  * Caller initialisation of a view: hash_keys all bits set (0xff bytes),
- * hash_vals -1 (0xff bytes), dist and weight zero, state zero.  The number of
- * allocated blocks is the first int32 of the state buffer; blocks are in
+ * hash_vals -1 (0xff bytes), dist and weight zero, state zero.  Alignment:
+ * dist and weight 16 bytes, hash_keys and state 8 bytes, hash_vals and
+ * block_keys 4 bytes; a misaligned view gives CVX_ERR_INVALID_ARG.  The
+ * number of allocated blocks is min(first int32 of the state buffer,
+ * max_blocks): after the pool overflowed the counter can exceed max_blocks,
+ * and the sticky error word (the int32 at byte offset 12 of the state) has
+ * bit 0 set (capacity; bit 1: key range, bit 2: timeout).  Blocks are in
  * allocation order in block_keys / dist / weight. */
 #define CVX_NOALLOC_MAX_BLOCKS 4096
 #define CVX_SUBMAP_STATE_BYTES 128

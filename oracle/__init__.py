@@ -57,7 +57,7 @@ def lib():
             L.orc_integrate.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp, i32]
             L.orc_extract.argtypes = [vp, vp, vp, vp]
             L.orc_block_set.restype = i64
-            L.orc_block_set.argtypes = [vp, vp, vp, i32, f32, f32, f32, f32, vp, vp, i64]
+            L.orc_block_set.argtypes = [vp, vp, vp, i32, f32, f32, f32, f32, vp, vp, vp, i64]
             L.orc_sampled.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, i32, i32, i32, f32, f32,
                                       vp, vp, i64, vp, vp, vp]
             L.orc_round_half.argtypes = [vp, i64, vp]
@@ -152,15 +152,25 @@ def _scan_arrays(scans: Sequence[np.ndarray], poses: Sequence[np.ndarray]):
     return pts, ptrs, counts, P
 
 
-def block_set(scans, poses, vs, trunc, min_range=0.1, max_range=1e9, sensors=None) -> np.ndarray:
-    """Sorted int32 [nb,3] keys of every block the scans' bands touch."""
+def _weight_ptrs(point_weights):
+    if point_weights is None:
+        return None, None
+    pwl = [_f32(w) for w in point_weights]
+    return pwl, (ctypes.c_void_p * len(pwl))(*[w.ctypes.data for w in pwl])
+
+
+def block_set(scans, poses, vs, trunc, min_range=0.1, max_range=1e9, sensors=None,
+              point_weights=None) -> np.ndarray:
+    """Sorted int32 [nb,3] keys of every block the scans' bands touch (with
+    per-point weights, points whose weight is not finite and >= 0 are dropped)."""
     pts, ptrs, counts, P = _scan_arrays(scans, poses)
     sens = np.ascontiguousarray(sensors if sensors is not None else np.zeros(len(pts)), dtype=np.int32)
+    pwl, pwp = _weight_ptrs(point_weights)
     n = lib().orc_block_set(ptrs, _p(counts), _p(P), len(pts), vs, trunc, min_range, max_range,
-                            _p(sens), None, 0)
+                            _p(sens), pwp, None, 0)
     keys = np.zeros((max(n, 1), 3), dtype=np.int32)
     lib().orc_block_set(ptrs, _p(counts), _p(P), len(pts), vs, trunc, min_range, max_range,
-                        _p(sens), _p(keys), n)
+                        _p(sens), pwp, _p(keys), n)
     return keys[:n]
 
 
@@ -173,10 +183,7 @@ def sampled(scans, poses, vox, vs, trunc, max_weight=1e4, fp16=False, weight_mod
     D, W = np.zeros(ns), np.zeros(ns)
     nobs = np.zeros(ns, dtype=np.int64)
     sens = np.ascontiguousarray(sensors if sensors is not None else np.zeros(len(pts)), dtype=np.int32)
-    pwp = None
-    if point_weights is not None:
-        pwl = [_f32(w) for w in point_weights]
-        pwp = (ctypes.c_void_p * len(pwl))(*[w.ctypes.data for w in pwl])
+    pwl, pwp = _weight_ptrs(point_weights)
     lib().orc_sampled(ptrs, _p(counts), _p(P), pwp, len(pts), vs, trunc, max_weight, int(fp16),
                       weight_mode, dropoff, min_range, max_range, _p(sens), _p(vox), ns, _p(D),
                       _p(W), _p(nobs))

@@ -195,6 +195,15 @@ double obs_weight(double base, double d, float vs, float trunc, int dropoff) {
   return base;
 }
 
+// A per-point weight must be a finite, non-negative number; a point whose
+// given weight is not is invalid like a point without a return (it is not
+// integrated and allocates nothing).
+bool point_weight_ok(const float* pw, int64_t i, int weight_mode) {
+  if (weight_mode != 2) return true;
+  const float w = pw[i];
+  return std::isfinite(w) && w >= 0.0f;
+}
+
 double base_weight(const float* ps, const Ray& ray, const float* pw, int64_t i, int weight_mode,
                    int sensor) {
   if (weight_mode == 0) return 1.0;
@@ -278,6 +287,7 @@ int orc_point_obs(const float* ps, const float* T, float vs, float trunc, float 
                   int32_t* vox, double* d, double* w, int cap, float* seg) {
   Ray ray;
   if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) return 0;
+  if (!point_weight_ok(&point_weight, 0, weight_mode)) return 0;
   float A[3], B[3];
   if (!band_segment(ray, trunc, vs, A, B)) return -2;
   if (seg) {
@@ -313,6 +323,7 @@ int orc_integrate(void* h, const float* pts, int64_t n, const float* T, const fl
     const float* ps = pts + 3 * i;
     Ray ray;
     if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) continue;
+    if (!point_weight_ok(pw, i, weight_mode)) continue;
     float A[3], B[3];
     if (!band_segment(ray, m->trunc, m->vs, A, B, carve != 0)) {
       ++bad;
@@ -376,10 +387,12 @@ void orc_extract(void* h, int32_t* keys, double* D, double* W) {
 
 /* Set of blocks touched by a sequence of scans (no voxel values).  keys_out
  * receives the sorted keys when it is non-NULL and cap suffices; returns the
- * number of distinct blocks. */
+ * number of distinct blocks.  point_weights (optional, one array per scan):
+ * per-point weights, whose invalid entries drop their points. */
 int64_t orc_block_set(const float* const* scans, const int64_t* counts, const float* poses,
                       int nscans, float vs, float trunc, float min_range, float max_range,
-                      const int* sensors, int32_t* keys_out, int64_t cap) {
+                      const int* sensors, const float* const* point_weights, int32_t* keys_out,
+                      int64_t cap) {
   std::unordered_set<Key, KeyHash> blocks;
   std::vector<Key> vox;
   for (int s = 0; s < nscans; ++s) {
@@ -388,6 +401,7 @@ int64_t orc_block_set(const float* const* scans, const int64_t* counts, const fl
       if (!make_ray(scans[s] + 3 * i, poses + 12 * s, min_range, max_range,
                     sensors ? sensors[s] : 0, &ray))
         continue;
+      if (point_weights && !point_weight_ok(point_weights[s], i, 2)) continue;
       float A[3], B[3];
       if (!band_segment(ray, trunc, vs, A, B)) continue;
       vox.clear();
@@ -438,6 +452,7 @@ void orc_sampled(const float* const* scans, const int64_t* counts, const float* 
       Ray ray;
       if (!make_ray(ps, poses + 12 * s, min_range, max_range, sensors ? sensors[s] : 0, &ray))
         continue;
+      if (!point_weight_ok(pw, i, weight_mode)) continue;
       float A[3], B[3];
       if (!band_segment(ray, trunc, vs, A, B)) continue;
       vv.clear();

@@ -218,6 +218,12 @@ __device__ __forceinline__ float base_weight(const ScanDev& sc, long long i, con
   return 1.0f / (z * z);
 }
 
+// A given per-point weight must be finite and non-negative; otherwise the
+// point is invalid (skipped like a point without a return).
+__device__ __forceinline__ bool weight_ok(const ScanDev& sc, float w0) {
+  return sc.weight_mode != 2 || (isfinite(w0) && w0 >= 0.0f);
+}
+
 __device__ __forceinline__ float dropoff_weight(float w, float d, float vs, float trunc, int mode) {
   if (mode != 0 && d < -vs) {
     float f = fmaxf((trunc + d) / (trunc - vs), 0.0f);

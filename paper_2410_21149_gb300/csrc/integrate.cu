@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "../../include/covox.h"
@@ -281,6 +282,34 @@ cvx_status flush_pending(cvx_submap* map, cudaStream_t s, bool discard) {
 // ===================================================================== C ABI
 namespace {
 
+// The per-scan kernels may use more than 48 KB of dynamic shared memory: the
+// attribute is per device, so it is set once for each device, with that
+// device current.
+constexpr int kMaxDevices = 64;
+std::mutex g_attr_mu;
+bool g_attr_set[kMaxDevices];
+
+cvx_status kernel_attributes() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_set[dev]) return CVX_OK;
+  const int bytes = (int)tile_smem_bytes(kMaxLocalBlocks);
+  for (int v = 0; v < 7; ++v)
+    if (cudaFuncSetAttribute((const void*)kIntegrate[v], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute((const void*)kPipelined[v], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return CVX_ERR_CUDA;
+    }
+  g_attr_set[dev] = true;
+  return CVX_OK;
+}
+
 void* sub_alloc(cvx_submap* m, size_t bytes) {
   void* ptr = nullptr;
   if (m->p.alloc) {
@@ -410,21 +439,8 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
   map->last_stream = s;
   if (n == 0) return CVX_OK;
   const size_t smem = tile_smem_bytes(lb);
-  static bool attr_set = false;
-  if (!attr_set) {
-    for (int v = 0; v < 7; ++v)
-      cudaFuncSetAttribute((const void*)kIntegrate[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)tile_smem_bytes(kMaxLocalBlocks));
-    attr_set = true;
-  }
+  if (kernel_attributes() != CVX_OK) return CVX_ERR_CUDA;
   if (map->pipelined) {
-    static bool pattr_set = false;
-    if (!pattr_set) {
-      for (int v = 0; v < 7; ++v)
-        cudaFuncSetAttribute((const void*)kPipelined[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tile_smem_bytes(kMaxLocalBlocks));
-      pattr_set = true;
-    }
     const int n_merge = num_sms();
     const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff, sc.carve) + 1];
     COVOX_LAUNCH(kKPipelined, s,

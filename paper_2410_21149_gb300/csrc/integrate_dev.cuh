@@ -351,7 +351,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
           const float zz = sc.sensor == 0 ? z3 * z3 : x * x + y * y + z3 * z3;
           w0 = 1.0f / zz;
         }
-        if (isfinite(w0)) wm = fmaxf(wm, fabsf(w0));
+        if (isfinite(w0) && w0 >= 0.0f) wm = fmaxf(wm, w0);   // other per-point weights drop their point
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
@@ -373,13 +373,14 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
     if (i < 0) continue;
     Ray r;
     if (!make_ray(sc, i, r)) continue;
+    const float w0 = base_weight(sc, i, r);
+    if (!weight_ok(sc, w0)) continue;
     float A[3], B[3];
     if (!band(r, m.trunc, m.inv_vs, A, B, kCarve)) {
       atomicOr(m.frame_err, kErrKeyRange);
       continue;
     }
     ++n_valid;
-    const float w0 = base_weight(sc, i, r);
     Dda d;
     d.init(A, B);
     n_obs += d.left + 1;

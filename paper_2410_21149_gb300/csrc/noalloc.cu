@@ -15,6 +15,7 @@
 // kernels.  Every GPU that loads this library holds the array until exit.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -116,6 +117,13 @@ extern "C" cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, co
       view->hash_slots > (1ll << 31) || view->max_blocks <= 0)
     return CVX_ERR_INVALID_ARG;
   if (!(view->voxel_size > 0) || !(view->trunc > 0) || !(view->max_weight > 0))
+    return CVX_ERR_INVALID_ARG;
+  // Vector loads and stores of D and W (16 bytes), 64-bit atomics on the hash
+  // keys and the state's counters: misaligned views are rejected here rather
+  // than faulting on the GPU.
+  const auto misaligned = [](const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; };
+  if (misaligned(view->dist, 16) || misaligned(view->weight, 16) || misaligned(view->hash_keys, 8) ||
+      misaligned(view->state, 8) || misaligned(view->hash_vals, 4) || misaligned(view->block_keys, 4))
     return CVX_ERR_INVALID_ARG;
   if (view->max_blocks > CVX_NOALLOC_MAX_BLOCKS) return CVX_ERR_CAPACITY;   // beyond the scratch
 

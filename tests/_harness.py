@@ -43,16 +43,17 @@ def run_gpu(wl: sg.Workload, storage=None, max_blocks=1 << 17, point_weights=Non
     return out
 
 
-def run_oracle(wl: sg.Workload, fp16=None, point_weights=None, carve=False):
+def run_oracle(wl: sg.Workload, fp16=None, point_weights=None, carve=False, weight_mode=None):
     import oracle as orc
     fp16 = bool(wl.storage) if fp16 is None else fp16
+    weight_mode = wl.weight_mode if weight_mode is None else weight_mode
     out = []
     for m, sm in enumerate(wl.submaps):
         om = orc.OracleSubmap(sm.voxel_size, sm.trunc, wl.max_weight, fp16)
         tot = {}
         for k, sc in enumerate(sm.scans):
             pw = None if point_weights is None else point_weights[m][k]
-            st = om.integrate(sc.points, sc.T_sub_sensor, pw, wl.weight_mode, wl.dropoff,
+            st = om.integrate(sc.points, sc.T_sub_sensor, pw, weight_mode, wl.dropoff,
                               wl.min_range, wl.max_range, sc.sensor, carve=carve)
             for key, v in st.items():
                 tot[key] = tot.get(key, 0) + v
@@ -93,7 +94,7 @@ def compare(gpu, orc, d_tol, w_rel=1e-4, w_floor=1e-6, fp16_trunc=None):
 
 
 def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=False, pipelined=False,
-                    wave_limit=0, **over):
+                    wave_limit=0, point_weights=None, **over):
     """Integrate all submaps of the workload with one cvx_integrate_batch call
     (scans of a submap are frames in order).  Returns the run_gpu tuple list."""
     import torch
@@ -112,7 +113,11 @@ def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=Fa
                 sc = sm.scans[k]
                 pts = torch.from_numpy(np.ascontiguousarray(sc.points)).cuda()
                 keep.append(pts)
-                scans.append((m, pts, sc.T_sub_sensor, None, int_params(wl, sc, **over)))
+                pw = None
+                if point_weights is not None:
+                    pw = torch.from_numpy(np.ascontiguousarray(point_weights[m][k], np.float32)).cuda()
+                    keep.append(pw)
+                scans.append((m, pts, sc.T_sub_sensor, pw, int_params(wl, sc, **over)))
         k += 1
     batch = _capi.cvx_batch_create(len(subs), len(scans))
     _capi.cvx_batch_wave_limit(batch, wave_limit)

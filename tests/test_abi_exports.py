@@ -42,3 +42,37 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     import pytest
     with pytest.raises(RuntimeError):
         _capi.lib()
+
+
+def test_noalloc_rejects_misaligned_views_on_the_host():
+    """The allocation-free entry point checks the caller's view before any
+    CUDA call: a pointer off its alignment (D and W 16 bytes, hash keys and
+    state 8, hash values and block keys 4) gives CVX_ERR_INVALID_ARG, and an
+    oversized view CVX_ERR_CAPACITY.  The pointers are never dereferenced."""
+    import numpy as np
+    from paper_2410_21149_gb300 import _build, _capi
+    _build.build()
+    L = _capi.lib()
+    T = np.eye(3, 4, dtype=np.float32).reshape(12)
+    prm = _capi.cvx_integrate_params(0, 0, 0.1, 1e9, 0, 0, 0, 0, 0, 0)
+
+    def view(**off):
+        base = {"hash_keys": 0x10000, "hash_vals": 0x20000, "block_keys": 0x30000, "dist": 0x40000,
+                "weight": 0x50000, "state": 0x60000}
+        v = _capi.cvx_submap_view()
+        for k, a in base.items():
+            setattr(v, k, a + off.get(k, 0))
+        v.hash_slots, v.max_blocks = 1024, 64
+        v.voxel_size, v.trunc, v.max_weight = 0.1, 0.3, 1e4
+        return v
+
+    def call(v):
+        return L.cvx_integrate_scan_noalloc(ctypes.byref(v), None, 0, T.ctypes.data_as(ctypes.c_void_p), None,
+                                            ctypes.byref(prm), None)
+
+    for field, off in (("dist", 4), ("weight", 8), ("hash_keys", 4), ("state", 4), ("hash_vals", 2),
+                       ("block_keys", 1)):
+        assert call(view(**{field: off})) == _capi.CVX_ERR_INVALID_ARG, field
+    big = view()
+    big.max_blocks = _capi.CVX_NOALLOC_MAX_BLOCKS + 1
+    assert call(big) == _capi.CVX_ERR_CAPACITY

@@ -110,3 +110,64 @@ def test_lidar_2000_scans_batched_full_size():
     _capi.cvx_batch_destroy(b)
     for s in subs:
         s.close()
+
+
+def test_batched_32_submaps_fp16_full_size():
+    """The batched workload at full size, as bench.py times it: 32 submaps of
+    1-16 scans mixing 640x480 pinhole frames and 64x1024 LiDAR scans, voxel
+    sizes 0.05 / 0.10 / 0.20 m, FP16 storage, pipelined submaps, one batched
+    persistent launch (256-point tiles, two shared block slots).  Every
+    submap's block set bit-exact; 3,000 sampled voxels per submap against the
+    oracle's FP16 storage mode (D within 1e-3 trunc, W within one half ulp)."""
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import _capi
+    wl = sg.make_c4()
+    assert len(wl.submaps) == 32
+    assert {s.width for sm in wl.submaps for s in sm.scans} == {640, 1024}
+    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, cvx.CVX_STORE_F16, max_blocks=1 << 16,
+                       pipelined=True) for sm in wl.submaps]
+    keep, scans = [], []
+    k = 0
+    while any(k < len(sm.scans) for sm in wl.submaps):
+        for m, sm in enumerate(wl.submaps):
+            if k < len(sm.scans):
+                sc = sm.scans[k]
+                p = torch.from_numpy(sc.points).cuda()
+                keep.append(p)
+                scans.append((m, p, sc.T_sub_sensor, None,
+                              cvx.integrate_params(0, 0, wl.min_range, wl.max_range, sc.sensor, sc.height,
+                                                   sc.width, 256, 2)))
+        k += 1
+    b = _capi.cvx_batch_create(len(subs), len(scans))
+    _capi.cvx_integrate_batch(b, [s.handle for s in subs], scans)
+    torch.cuda.synchronize()
+    assert _capi.cvx_batch_error(b) == 0
+    rng = np.random.default_rng(4)
+    checked = 0
+    for m, (sm, sub) in enumerate(zip(wl.submaps, subs)):
+        assert sub.status() == 0
+        keys, D, W = (t.cpu().numpy() for t in sub.extract())
+        D = D.astype(np.float64) * np.float64(np.float32(sm.trunc))
+        W = W.astype(np.float64)
+        pts = [s.points for s in sm.scans]
+        poses = [s.T_sub_sensor for s in sm.scans]
+        sensors = [s.sensor for s in sm.scans]
+        ko = orc.block_set(pts, poses, sm.voxel_size, sm.trunc, wl.min_range, wl.max_range, sensors)
+        kg, Dg, Wg = sort_blocks(keys, D, W)
+        assert np.array_equal(kg, ko), f"block sets differ (submap {m})"
+        bb, ll, vox = _sample(kg, Wg, rng)
+        Do, Wo, _ = orc.sampled(pts, poses, vox, sm.voxel_size, sm.trunc, wl.max_weight, True, 0, 0,
+                                wl.min_range, wl.max_range, sensors)
+        dg, wg = Dg[bb, ll], Wg[bb, ll]
+        ulp = np.exp2(np.floor(np.log2(np.maximum(np.abs(Wo), 2.0 ** -14))) - 10)
+        assert (np.abs(wg - Wo) <= ulp + W_FLOOR).all(), f"W (submap {m})"
+        both = (Wo > W_FLOOR) & (wg > W_FLOOR)
+        assert np.abs(dg - Do)[both].max() <= 1e-3 * sm.trunc, f"D (submap {m})"
+        assert both.sum() >= min(3000, int((Wg > 0).sum()))
+        checked += int(both.sum())
+        assert sub.counters()["frames"] == len(sm.scans)
+    assert checked > 32 * 2500
+    _capi.cvx_batch_destroy(b)
+    for s in subs:
+        s.close()

@@ -132,3 +132,31 @@ def test_targets_zero_for_the_integrated_point_and_shift_squared():
     d_clean = np.array([0.25, 0.125, 0.0, -0.125, -0.25, -0.375])
     d_new = np.clip(d_clean + 0.0625, -tr, tr)
     assert mask[0] and abs(e2[0] - np.mean((d_new - d_clean) ** 2)) < 1e-15
+
+
+def test_adam_two_steps_hand_derived():
+    """The oracle's Adam against a two-step sequence worked out by hand with
+    exact fractions (tests/golden/adam_two_steps.json)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "adam_two_steps.json")) as f:
+        gold = json.load(f)
+    opt = mlp.Adam(1, lr=gold["lr"], b1=gold["b1"], b2=gold["b2"], eps=gold["eps"])
+    theta = np.array([gold["theta0"]])
+    for g, expect in zip(gold["grads"], gold["theta"]):
+        theta = opt.step(theta, np.array([g]))
+        assert abs(theta[0] - expect) < 1e-15
+
+
+def test_adam_constant_gradient_closed_form():
+    """With a constant gradient g the bias corrections cancel exactly
+    (m^ = g, v^ = g^2 at every step), so each step moves theta by
+    lr g / (|g| + eps): after t steps theta = theta0 - t lr g / (|g| + eps)."""
+    rng = np.random.default_rng(3)
+    g = rng.normal(0, 2, 50)
+    theta0 = rng.normal(0, 1, 50)
+    opt = mlp.Adam(50, lr=1e-2)
+    theta = theta0.copy()
+    for t in range(1, 8):
+        theta = opt.step(theta, g)
+        assert np.allclose(theta, theta0 - t * 1e-2 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-13)

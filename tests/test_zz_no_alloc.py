@@ -79,6 +79,12 @@ def test_noalloc_matches_regular_entry_point_two_scans():
     assert np.abs(Dn - Dr)[both].max() <= D_TOL
     assert both.sum() > 10000
 
+    # and directly against the CPU oracle (the same two frames)
+    from _harness import compare, run_oracle
+    wl.submaps[0].scans = scans
+    orc = run_oracle(wl)[0]
+    compare((kn, Dn, Wn, {}, 0), orc, D_TOL)
+
 
 def test_noalloc_rejects_views_beyond_the_scratch():
     torch = pytest.importorskip("torch")
