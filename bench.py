@@ -525,6 +525,9 @@ def run_ours(args):
         "config": {"workload": wl.name, "frames_per_step": F, "points_per_frame": N,
                    "voxel_size_m": sm.voxel_size, "trunc_m": sm.trunc, "weight": "quadratic+linear-dropoff",
                    "storage": "f32", "step": "clear submap + integrate all frames (CUDA graph replay)",
+                   "launch_shape": "%d points per CTA, %s, %s submap" % (
+                       args.ppc, "L2 vector reductions" if args.lb < 0 else f"{args.lb or 8} shared block slots",
+                       "pipelined" if pipelined else "plain"),
                    "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb, "pipelined": pipelined,
                                  "candidates_ms_20_frames": tune_report},
                    "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (F * N * 12 / 1e6),
@@ -558,6 +561,8 @@ def run_ours(args):
         out["forms"]["hash_stress"] = hash_stress_form(args)
     if not args.no_learned:
         out["forms"]["learned_weight"] = learned_form(wl, pts, Ts, stream, args, ws, rmse32, ms32 / args.steps)
+    if not args.no_lidar:
+        out["forms"]["lidar"] = lidar_form(args, ws, rank, peaks, peak_src)
     if not args.no_batched:
         import scenegen as sg
         wl4 = sg.make_c4()
@@ -573,6 +578,10 @@ def run_ours(args):
             "batched_kernel_gbs": r4["kernel_bytes"] / (r4["batched_kernel_ms"] / 1e3) / 1e9}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+        out["cpu_baseline_parallel"] = cpu_baseline_parallel(wl, args.cpu_seconds / 2)
+        err = storage_error_vs_oracle(wl, params, stream, frames=args.error_frames)
+        out["forms"]["fp16_storage"]["error_vs_fp64_oracle"] = err["fp16"]
+        out["error_fp32_vs_fp64_oracle"] = err["fp32"]
     if rank == 0:
         print(json.dumps(out), flush=True)
     for s in (sub32, sub16):
@@ -755,37 +764,30 @@ def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):
     _capi.cvx_profile_stop()
     prof = _capi.cvx_profile_read()
     sub.close()
+    gain = weighting_noise_rmse(model, wl, stream)
     model.close()
     return {"points_per_s": sum_over_ranks(c["valid_points"], ws) / (ms / 1e3),
             "ms_per_step": ms, "speedup_vs_fp32": ms_plain / ms, "sdf_rmse_m": rmse_l, "sdf_rmse_plain_quadratic_m": rmse_plain,
             "gate_keeps_learned": bool(weights.gate(rmse_l, rmse_plain)),
+            "noise_rmse_vs_noise_free_fusion": gain,
             "training": {"points": int(F.shape[0]), "steps": 1500, "batch": 65536,
                          "loss_first50": float(np.mean(losses[:50])), "loss_last50": float(np.mean(losses[-50:])),
                          "data_s": t1 - t0, "train_s": t2 - t1},
             "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]}}
 
 
-def run_lidar(args, ws, rank, peaks, peak_src):
-    """LiDAR/MAV workload: 64x1024 scans along a 400 m loop, a submap per 50
-    scans; one batched persistent launch per step (all submaps' scans)."""
+def lidar_numbers(args, ws, peaks, peak_src, storage=0, n_scans=2000):
+    """LiDAR/MAV workload (64x1024 scans along a 400 m loop, a submap per 50
+    scans) through one batched persistent launch per step; the per-scan path
+    and the end-to-end copy-in timing beside it."""
     import scenegen as sg
-    wl = sg.make_c3(n_scans=args.scans)
+    wl = sg.make_c3(n_scans=n_scans)
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    clocks = Clocks(0)
-    clocks.start()
-    r = bench_multi(wl, 0, args.steps, args.warmup, ws, max_blocks=1 << 16)
-    clk = clocks.stop()
+    r = bench_multi(wl, storage, args.steps, args.warmup, ws, max_blocks=1 << 16)
     pts = sum_over_ranks(r["points"], ws)
     ach = r["kernel_bytes"] / (r["batched_kernel_ms"] / 1e3) / 1e9
-    out = {
-        "metric": "TSDF integration points/s (LiDAR, batched persistent FP32, 1 GB300)",
-        "value": pts / (r["ms_per_step"] / 1e3), "unit": "points/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "submaps": r["submaps"], "scans": r["scans"],
-                   "step": "clear all submaps + one batched launch over all scans (CUDA graph replay)",
-                   "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (r["input_points"] * 12 / 1e6),
-                   "parallelism": f"replica x{ws}"},
+    return wl, r, {
+        "points_per_s": pts / (r["ms_per_step"] / 1e3), "ms_per_step": r["ms_per_step"],
         "voxel_updates_per_s": sum_over_ranks(r["observations"], ws) / (r["ms_per_step"] / 1e3),
         "unique_voxel_merges_per_s": sum_over_ranks(r["voxels_merged"], ws) / (r["ms_per_step"] / 1e3),
         "sdf_rmse_m": r["sdf_rmse_m"],
@@ -796,16 +798,111 @@ def run_lidar(args, ws, rank, peaks, peak_src):
                      "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": r["kernel_bytes"], "avg_launch_ms": r["batched_kernel_ms"]},
         "counts_per_step": {k: r[k] for k in ("points", "observations", "voxels_merged", "blocks_touched",
-                                              "blocks_allocated")},
-        "block_granular_bytes_per_step": 2 * 8 * 512 * r["blocks_touched"],
+                                              "blocks_allocated", "input_points")},
+        "block_granular_bytes_per_step": 2 * (8 if storage == 0 else 4) * 512 * r["blocks_touched"],
         "autotuned": r["tuned"], "batched_phases": r["phases"],
         "e2e": {"value": pts / (r["e2e_ms_per_step"] / 1e3), "unit": "points/s",
                 "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"]},
-        "gpu_launches": r["launches_per_step"] * args.steps, "gpu_launches_per_step": r["launches_per_step"],
+        "gpu_launches_per_step": r["launches_per_step"],
+    }
+
+
+def lidar_form(args, ws, rank, peaks, peak_src):
+    """The LiDAR/MAV workload beside the headline: FP32 (its own roofline,
+    e2e, per-scan path) and FP16 storage, with the oracle on a bounded
+    prefix."""
+    wl, r, res = lidar_numbers(args, ws, peaks, peak_src, storage=0)
+    res["workload"] = wl.name + " (40 submaps of 50 scans, batched persistent launch, FP32)"
+    _, r16, res16 = lidar_numbers(args, ws, peaks, peak_src, storage=1)
+    res["fp16_storage"] = {"points_per_s": res16["points_per_s"], "ms_per_step": res16["ms_per_step"],
+                           "speedup_vs_fp32": res["ms_per_step"] / res16["ms_per_step"],
+                           "sdf_rmse_m": res16["sdf_rmse_m"], "roofline": res16["roofline"],
+                           "autotuned": res16["autotuned"]}
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        res["cpu_baseline"] = cpu_baseline(sub_workload(wl, 1), args.cpu_seconds / 2)
+        res["cpu_baseline_parallel"] = cpu_baseline_submaps(wl, args.cpu_seconds / 2)
+    return res
+
+
+def sub_workload(wl, n_submaps):
+    import copy
+    w = copy.copy(wl)
+    w.submaps = wl.submaps[:n_submaps]
+    return w
+
+
+def weighting_noise_rmse(model, wl, stream, seeds=(33, 35, 37), frames=40):
+    """The gain the weight network is trained for, on held-out buildings: the
+    RMS difference between the TSDF fused from noisy scans and the TSDF fused
+    from the same scans without noise (same per-ray weights), for constant,
+    quadratic and learned weighting with the workload's drop-off; per seed
+    and as mean and spread over the seeds."""
+    import torch
+    import scenegen as sg
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import weights
+    sm0 = wl.submaps[0]
+    H, W = sm0.scans[0].height, sm0.scans[0].width
+    per = {m: [] for m in ("constant", "quadratic", "learned")}
+    for seed in seeds:
+        noisy = sg.make_c2(seed=seed, n_frames=frames, width=W, height=H).submaps[0]
+        clean = sg.make_c2(seed=seed, n_frames=frames, width=W, height=H, noise=False).submaps[0]
+        npts = [torch.from_numpy(sc.points).cuda() for sc in noisy.scans]
+        cpts = [torch.from_numpy(sc.points).cuda() for sc in clean.scans]
+        lw = [weights.learned_point_weights(model, p, H, W, 0, wl.max_range) for p in npts]
+        for mode, wm in (("constant", 0), ("quadratic", 1), ("learned", 2)):
+            prm = cvx.integrate_params(wm, wl.dropoff, wl.min_range, wl.max_range, 0, H, W)
+            out = []
+            for pts in (npts, cpts):
+                with torch.cuda.stream(stream):
+                    sub = cvx.Submap(sm0.voxel_size, sm0.trunc, wl.max_weight, 0, max_blocks=1 << 17, stream=stream)
+                for f, sc in enumerate(noisy.scans):
+                    # learned: the noisy rays' weights serve both fusions
+                    sub.integrate(pts[f], sc.T_sub_sensor, prm, lw[f] if wm == 2 else None, stream)
+                out.append(tuple(t.cpu().numpy() for t in sub.extract(stream)))
+                sub.close()
+            (kn, Dn, Wn), (kc, Dc, Wc) = out
+            lut = {tuple(k): b for b, k in enumerate(kc)}
+            diffs = []
+            for b, k in enumerate(kn):
+                bc = lut.get(tuple(k))
+                if bc is None:
+                    continue
+                m = (Wn[b] > 0) & (Wc[bc] > 0) & (np.abs(Dn[b]) < sm0.trunc)
+                diffs.append((Dn[b] - Dc[bc])[m].astype(np.float64))
+            per[mode].append(float(np.sqrt(np.mean(np.concatenate(diffs) ** 2))))
+    return {"seeds": list(seeds), "frames": frames,
+            "per_seed_m": per,
+            "mean_m": {m: float(np.mean(v)) for m, v in per.items()},
+            "spread_m": {m: float(np.std(v)) for m, v in per.items()},
+            "learned_vs_quadratic": [l / q for l, q in zip(per["learned"], per["quadratic"])]}
+
+
+def run_lidar(args, ws, rank, peaks, peak_src):
+    """`--workload lidar`: the LiDAR form as the headline line."""
+    clocks = Clocks(0)
+    clocks.start()
+    wl, r, res = lidar_numbers(args, ws, peaks, peak_src, storage=0, n_scans=args.scans)
+    clk = clocks.stop()
+    out = {
+        "metric": "TSDF integration points/s (LiDAR, batched persistent FP32, 1 GB300)",
+        "value": res["points_per_s"], "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "submaps": r["submaps"], "scans": r["scans"],
+                   "step": "clear all submaps + one batched launch over all scans (CUDA graph replay)",
+                   "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (r["input_points"] * 12 / 1e6),
+                   "launch_shape": r["tuned"], "parallelism": f"replica x{ws}"},
+        "gpu_launches": r["launches_per_step"] * args.steps,
         "clocks": clk,
     }
+    for k in ("voxel_updates_per_s", "unique_voxel_merges_per_s", "sdf_rmse_m", "per_scan_path", "roofline",
+              "counts_per_step", "block_granular_bytes_per_step", "batched_phases", "e2e",
+              "gpu_launches_per_step"):
+        out[k] = res[k]
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        out["cpu_baseline"] = cpu_baseline(sg.make_c3(n_scans=50), args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(sub_workload(wl, 1), args.cpu_seconds)
+        out["cpu_baseline_parallel"] = cpu_baseline_submaps(wl, args.cpu_seconds / 2)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -831,6 +928,120 @@ def cpu_baseline(wl, seconds: float):
     return {"value": valid / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
             "voxel_updates_per_s": obs / dt,
             "sample": f"first {frames} of {len(sm.scans)} frames of {wl.name} ({valid} valid points, {dt:.1f} s)"}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline_parallel(wl, seconds: float):
+    """The oracle with each frame's sums accumulated by all host cores (OpenMP
+    over point chunks, chunk sums added in order) on the first frames of the
+    same workload."""
+    import oracle as orc
+    threads = os.cpu_count() or 1
+    sm = wl.submaps[0]
+    om = orc.OracleSubmap(sm.voxel_size, sm.trunc, wl.max_weight, bool(wl.storage))
+    t0 = time.perf_counter()
+    valid = obs = frames = 0
+    for sc in sm.scans:
+        st = om.integrate_parallel(sc.points, sc.T_sub_sensor, threads, None, wl.weight_mode, wl.dropoff,
+                                   wl.min_range, wl.max_range, sc.sensor)
+        valid += st["valid"]
+        obs += st["obs"]
+        frames += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": valid / dt, "unit": "points/s", "cores": threads, "kind": "oracle, OpenMP over point chunks",
+            "cpu_model": cpu_model(), "voxel_updates_per_s": obs / dt,
+            "sample": f"first {frames} of {len(sm.scans)} frames of {wl.name} ({valid} valid points, {dt:.1f} s)"}
+
+
+def cpu_baseline_submaps(wl, seconds: float):
+    """The oracle on independent submaps at once, one host thread per submap
+    (the oracle's calls release the interpreter lock), on the first submaps
+    of the workload."""
+    import concurrent.futures as cf
+    import oracle as orc
+    threads = min(os.cpu_count() or 1, len(wl.submaps))
+    budget = seconds
+
+    def one(sm):
+        om = orc.OracleSubmap(sm.voxel_size, sm.trunc, wl.max_weight, bool(wl.storage))
+        t0 = time.perf_counter()
+        v = n = 0
+        for sc in sm.scans:
+            st = om.integrate(sc.points, sc.T_sub_sensor, None, wl.weight_mode, wl.dropoff, wl.min_range,
+                              wl.max_range, sc.sensor)
+            v += st["valid"]
+            n += 1
+            if time.perf_counter() - t0 > budget:
+                break
+        return v, n
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(one, wl.submaps[:threads]))
+    dt = time.perf_counter() - t0
+    valid = sum(v for v, _ in res)
+    scans = sum(n for _, n in res)
+    return {"value": valid / dt, "unit": "points/s", "cores": threads, "kind": "oracle, one thread per submap",
+            "cpu_model": cpu_model(),
+            "sample": f"first scans of {threads} of {len(wl.submaps)} submaps of {wl.name} ({scans} scans, "
+                      f"{valid} valid points, {dt:.1f} s)"}
+
+
+def storage_error_vs_oracle(wl, params, stream, frames: int = 10):
+    """D and W of the GPU path (FP32 storage, and FP16 storage with FP32
+    accumulation) after the first `frames` frames of the workload, against the
+    FP64 oracle without storage rounding: max and RMS |dD| over voxels with
+    W > 0, max relative |dW|."""
+    import torch
+    import oracle as orc
+    import paper_2410_21149_gb300 as cvx
+    sm = wl.submaps[0]
+    om = orc.OracleSubmap(sm.voxel_size, sm.trunc, wl.max_weight, False)
+    for sc in sm.scans[:frames]:
+        om.integrate(sc.points, sc.T_sub_sensor, None, wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range,
+                     sc.sensor)
+    ko, Do, Wo = om.extract()
+    res = {}
+    for name, storage in (("fp32", 0), ("fp16", 1)):
+        with torch.cuda.stream(stream):
+            sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=1 << 16, stream=stream)
+        for sc in sm.scans[:frames]:
+            sub.integrate(torch.from_numpy(sc.points).cuda(), sc.T_sub_sensor, params, None, stream)
+        keys, D, W = (t.cpu().numpy() for t in sub.extract(stream))
+        sub.close()
+        D = D.astype(np.float64) * (np.float64(np.float32(sm.trunc)) if storage else 1.0)
+        W = W.astype(np.float64)
+        order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+        keys, D, W = keys[order], D[order], W[order]
+        if not np.array_equal(keys, ko):
+            res[name] = {"error": "block sets differ"}
+            continue
+        m = Wo > 1e-6
+        dD = np.abs(D - Do)[m]
+        dW = (np.abs(W - Wo) / np.maximum(Wo, 1e-6))[m]
+        res[name] = {"frames": frames, "voxels": int(m.sum()), "max_abs_dD_m": float(dD.max()),
+                     "rms_dD_m": float(np.sqrt(np.mean(dD ** 2))), "max_rel_dW": float(dW.max()),
+                     "max_abs_dD_over_trunc": float(dD.max() / sm.trunc)}
+    return res
 
 
 def run_reference(args):
@@ -872,6 +1083,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-weight form (multiroom)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the carving, ESDF and hash-stress forms (multiroom)")
+    ap.add_argument("--no-lidar", action="store_true", help="skip the LiDAR form (multiroom)")
+    ap.add_argument("--error-frames", type=int, default=10,
+                    help="frames of the storage-error comparison against the oracle (CPU leg)")
     ap.add_argument("--frames", type=int, default=200)
     ap.add_argument("--ppc", type=int, default=0, help="points per CTA tile (0: autotuned)")
     ap.add_argument("--lb", type=int, default=0, help="shared block slots per CTA (-1: global atomics)")

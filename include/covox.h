@@ -157,7 +157,8 @@ cvx_status cvx_extract_blocks(cvx_submap* map, int64_t capacity, int32_t* keys, 
                               void* weight, int64_t* n_out, void* stream);
 
 /* Clear all blocks and counters (asynchronous, no host synchronisation).  A
- * scan still pending in a pipelined submap is dropped. */
+ * scan still pending in a pipelined submap is dropped, and so are the
+ * per-scan sums a launch that gave up (CVX_ERR_TIMEOUT) left unmerged. */
 cvx_status cvx_reset_submap(cvx_submap* map, void* stream);
 
 /* Pipelined submap: merge the scan the last cvx_integrate_scan() left
@@ -289,6 +290,15 @@ cvx_status cvx_batch_wave_limit(cvx_batch* batch, int32_t max_scans_per_wave);
 /* CVX_ERR_TIMEOUT if a barrier of the last batch gave up (synchronous). */
 int32_t cvx_batch_error(cvx_batch* batch);
 
+/* Test hook for the bounded grid barriers (off by default): while
+ * missing_cta >= 0, that CTA of this batch's launches leaves before its first
+ * barrier arrival, and the barriers give up after barrier_polls polls
+ * (<= 0: the default limit, about one second).  The other CTAs then wait out
+ * the limit and return; cvx_batch_error() reports CVX_ERR_TIMEOUT and the
+ * submaps must be reset.  missing_cta < 0 restores normal launches.  Nothing
+ * faults or hangs: it exercises the timeout path the barriers always have. */
+cvx_status cvx_batch_test_missing_cta(cvx_batch* batch, int32_t missing_cta, int64_t barrier_polls);
+
 void cvx_batch_destroy(cvx_batch* batch);
 
 /* Tracing of the batched kernel: with timing enabled, CTA 0 stamps the GPU
@@ -345,6 +355,14 @@ cvx_status cvx_training_targets(cvx_submap* clean, const float* points_xyz, int6
                                 const float T_sub_sensor[12], const cvx_integrate_params* params,
                                 float* e2, float* mask, void* stream);
 
+/* Scale of a training set's targets: e2[i] /= mean, mean = sum(e2 mask) /
+ * max(sum(mask), 1), in place on the device (fixed-order reduction, so the
+ * result does not depend on scheduling); *mean_out (host) receives the mean.
+ * The fitted weights are then ~1 for a typical point, the scale of the
+ * constant weight, so the stored weight's cap is met no sooner than with the
+ * plain weighting.  Synchronises `stream`. */
+cvx_status cvx_normalise_targets(float* e2, const float* mask, int64_t n, float* mean_out, void* stream);
+
 /* ---- integration without device allocation ----
  * No counterpart in the paper: an addition for callers that cannot allocate
  * device memory -- a real-time loop that must never allocate after start-up,
@@ -355,7 +373,7 @@ cvx_status cvx_training_targets(cvx_submap* clean, const float* points_xyz, int6
  * and results as cvx_integrate_scan() on float32 storage, into submap storage
  * the caller owns and describes with a cvx_submap_view.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.  Its per-scan scratch
- * (per-voxel sums and touched-block list, about 16.1 MiB) is one fixed array
+ * (per-voxel sums and the blocks' touch epochs, about 16 MiB) is one fixed array
  * in device memory that every GPU loading this library holds until the
  * process exits.
  *   - The first call on a device, with that device current, looks up the

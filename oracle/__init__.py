@@ -31,7 +31,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC])
+                               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC])
         os.replace(tmp, _SO)
     return _SO
 
@@ -55,6 +55,8 @@ def lib():
                                         i32, vp]
             L.orc_integrate.restype = i32
             L.orc_integrate.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp, i32]
+            L.orc_integrate_parallel.restype = i32
+            L.orc_integrate_parallel.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp, i32, i32]
             L.orc_extract.argtypes = [vp, vp, vp, vp]
             L.orc_block_set.restype = i64
             L.orc_block_set.argtypes = [vp, vp, vp, i32, f32, f32, f32, f32, vp, vp, vp, i64]
@@ -96,6 +98,25 @@ class OracleSubmap:
         stats = np.zeros(6, dtype=np.int64)
         rc = lib().orc_integrate(self.h, _p(pts), len(pts), _p(Tm), _p(pw), weight_mode, dropoff,
                                  min_range, max_range, sensor, _p(stats), 1 if carve else 0)
+        keys = ("valid", "obs", "voxels", "blocks", "new_blocks", "key_range")
+        out = dict(zip(keys, (int(x) for x in stats)))
+        out["status"] = rc
+        return out
+
+    def integrate_parallel(self, points: np.ndarray, T: np.ndarray, threads: int,
+                           point_weights: Optional[np.ndarray] = None, weight_mode: int = 0, dropoff: int = 0,
+                           min_range: float = 0.1, max_range: float = 1e9, sensor: int = 0,
+                           carve: bool = False) -> Dict[str, int]:
+        """One frame with its sums accumulated by `threads` threads over point
+        chunks (chunk maps added in chunk order): integrate() up to FP64
+        rounding, for the timed parallel CPU baseline."""
+        pts = _f32(points).reshape(-1, 3)
+        Tm = _f32(T).reshape(12)
+        pw = None if point_weights is None else _f32(point_weights)
+        stats = np.zeros(6, dtype=np.int64)
+        rc = lib().orc_integrate_parallel(self.h, _p(pts), len(pts), _p(Tm), _p(pw), weight_mode, dropoff,
+                                          min_range, max_range, sensor, _p(stats), 1 if carve else 0,
+                                          int(threads))
         keys = ("valid", "obs", "voxels", "blocks", "new_blocks", "key_range")
         out = dict(zip(keys, (int(x) for x in stats)))
         out["status"] = rc

@@ -250,6 +250,73 @@ void merge_voxel(Map* m, Block& b, int l, double swd, double sw) {
   b.W[l] = Wc;
 }
 
+using FrameSums = std::map<Key, std::pair<double, double>>;
+
+struct FrameCounts {
+  int64_t valid = 0, nobs = 0, bad = 0;
+};
+
+// Observations of points [i0, i1) of one scan, summed per voxel in point
+// order into `frame` (weighted distance, weight).
+void accumulate_points(const Map* m, const float* pts, int64_t i0, int64_t i1, const float* T,
+                       const float* pw, int weight_mode, int dropoff, float min_range,
+                       float max_range, int sensor, int carve, FrameSums* frame, FrameCounts* cnt) {
+  std::vector<Key> vox;
+  for (int64_t i = i0; i < i1; ++i) {
+    const float* ps = pts + 3 * i;
+    Ray ray;
+    if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) continue;
+    if (!point_weight_ok(pw, i, weight_mode)) continue;
+    float A[3], B[3];
+    if (!band_segment(ray, m->trunc, m->vs, A, B, carve != 0)) {
+      ++cnt->bad;
+      continue;
+    }
+    ++cnt->valid;
+    vox.clear();
+    traverse(A, B, &vox);
+    double base = base_weight(ps, ray, pw, i, weight_mode, sensor);
+    for (const Key& v : vox) {
+      double d = voxel_distance(ray, v, m->vs, m->trunc);
+      double w = obs_weight(base, d, m->vs, m->trunc, dropoff);
+      auto& acc = (*frame)[v];
+      acc.first += w * d;
+      acc.second += w;
+      ++cnt->nobs;
+    }
+  }
+}
+
+// End of a frame: allocate every block an observation fell in (even with zero
+// weight), then, unless a point left the key range, merge each voxel's sums.
+int apply_frame(Map* m, const FrameSums& frame, const FrameCounts& cnt, int64_t* stats) {
+  std::map<Key, int> touched;
+  int64_t newb = 0;
+  for (auto& kv : frame) {
+    Key b = block_of(kv.first);
+    if (touched.emplace(b, 1).second && m->blocks.find(b) == m->blocks.end()) {
+      Block& blk = m->blocks[b];
+      std::memset(&blk, 0, sizeof(Block));
+      ++newb;
+    }
+  }
+  if (cnt.bad == 0) {
+    for (auto& kv : frame) {
+      Block& blk = m->blocks[block_of(kv.first)];
+      merge_voxel(m, blk, local_of(kv.first), kv.second.first, kv.second.second);
+    }
+  }
+  if (stats) {
+    stats[0] = cnt.valid;
+    stats[1] = cnt.nobs;
+    stats[2] = (int64_t)frame.size();
+    stats[3] = (int64_t)touched.size();
+    stats[4] = newb;
+    stats[5] = cnt.bad;
+  }
+  return cnt.bad ? -4 : 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -305,6 +372,7 @@ int orc_point_obs(const float* ps, const float* T, float vs, float trunc, float 
   return (int)v.size();
 }
 
+
 /* Integrate one scan (one frame).  pts: [n,3] sensor frame; T: 3x4 row-major
  * submap <- sensor; pw: per-point weights (weight_mode 2) or NULL.
  * stats (optional, 6 entries): valid points, observations, unique voxels,
@@ -315,59 +383,43 @@ int orc_integrate(void* h, const float* pts, int64_t n, const float* T, const fl
                   int weight_mode, int dropoff, float min_range, float max_range, int sensor,
                   int64_t* stats, int carve) {
   Map* m = (Map*)h;
-  // Frame sums keyed by voxel, accumulated in point-index order.
-  std::map<Key, std::pair<double, double>> frame;
-  int64_t valid = 0, nobs = 0, bad = 0;
-  std::vector<Key> vox;
-  for (int64_t i = 0; i < n; ++i) {
-    const float* ps = pts + 3 * i;
-    Ray ray;
-    if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) continue;
-    if (!point_weight_ok(pw, i, weight_mode)) continue;
-    float A[3], B[3];
-    if (!band_segment(ray, m->trunc, m->vs, A, B, carve != 0)) {
-      ++bad;
-      continue;
-    }
-    ++valid;
-    vox.clear();
-    traverse(A, B, &vox);
-    double base = base_weight(ps, ray, pw, i, weight_mode, sensor);
-    for (const Key& v : vox) {
-      double d = voxel_distance(ray, v, m->vs, m->trunc);
-      double w = obs_weight(base, d, m->vs, m->trunc, dropoff);
-      auto& acc = frame[v];
-      acc.first += w * d;
-      acc.second += w;
-      ++nobs;
-    }
+  FrameSums frame;   // frame sums keyed by voxel, accumulated in point-index order
+  FrameCounts cnt;
+  accumulate_points(m, pts, 0, n, T, pw, weight_mode, dropoff, min_range, max_range, sensor, carve,
+                    &frame, &cnt);
+  return apply_frame(m, frame, cnt, stats);
+}
+
+/* The same frame with its sums accumulated by `threads` OpenMP threads, each
+ * over a contiguous chunk of the points into its own map; the chunk maps are
+ * then added in chunk order.  The result differs from orc_integrate only by
+ * the FP64 rounding of the sums' order.  The parallel CPU baseline. */
+int orc_integrate_parallel(void* h, const float* pts, int64_t n, const float* T, const float* pw,
+                           int weight_mode, int dropoff, float min_range, float max_range,
+                           int sensor, int64_t* stats, int carve, int threads) {
+  Map* m = (Map*)h;
+  if (threads < 1) threads = 1;
+  std::vector<FrameSums> part(threads);
+  std::vector<FrameCounts> pc(threads);
+#pragma omp parallel for num_threads(threads) schedule(static, 1)
+  for (int t = 0; t < threads; ++t) {
+    const int64_t i0 = n * t / threads, i1 = n * (t + 1) / threads;
+    accumulate_points(m, pts, i0, i1, T, pw, weight_mode, dropoff, min_range, max_range, sensor,
+                      carve, &part[t], &pc[t]);
   }
-  // Allocate every block any observation falls in (even with zero weight).
-  std::map<Key, int> touched;
-  int64_t newb = 0;
-  for (auto& kv : frame) {
-    Key b = block_of(kv.first);
-    if (touched.emplace(b, 1).second && m->blocks.find(b) == m->blocks.end()) {
-      Block& blk = m->blocks[b];
-      std::memset(&blk, 0, sizeof(Block));
-      ++newb;
+  FrameSums frame = std::move(part[0]);
+  FrameCounts cnt = pc[0];
+  for (int t = 1; t < threads; ++t) {
+    for (auto& kv : part[t]) {
+      auto& acc = frame[kv.first];
+      acc.first += kv.second.first;
+      acc.second += kv.second.second;
     }
+    cnt.valid += pc[t].valid;
+    cnt.nobs += pc[t].nobs;
+    cnt.bad += pc[t].bad;
   }
-  if (bad == 0) {
-    for (auto& kv : frame) {
-      Block& blk = m->blocks[block_of(kv.first)];
-      merge_voxel(m, blk, local_of(kv.first), kv.second.first, kv.second.second);
-    }
-  }
-  if (stats) {
-    stats[0] = valid;
-    stats[1] = nobs;
-    stats[2] = (int64_t)frame.size();
-    stats[3] = (int64_t)touched.size();
-    stats[4] = newb;
-    stats[5] = bad;
-  }
-  return bad ? -4 : 0;
+  return apply_frame(m, frame, cnt, stats);
 }
 
 /* Copy out all blocks in ascending key order: keys [nb,3], D and W [nb,512]

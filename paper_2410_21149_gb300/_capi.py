@@ -110,6 +110,7 @@ SIGNATURES = {
     "cvx_batch_destroy": (None, [_vp]),
     "cvx_batch_timing": (_i32, [_vp, _i32]),
     "cvx_batch_wave_limit": (_i32, [_vp, _i32]),
+    "cvx_batch_test_missing_cta": (_i32, [_vp, _i32, _i64]),
     "cvx_batch_phase_times": (_i32, [_vp, _vp, _i32]),
     "cvx_point_features": (_i32, [_vp, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "cvx_weight_model_create": (_i32, [_vp, ctypes.POINTER(_vp)]),
@@ -119,6 +120,7 @@ SIGNATURES = {
     "cvx_weight_model_last": (_i32, [_vp, _vp, _vp, _vp]),
     "cvx_weight_model_destroy": (None, [_vp]),
     "cvx_training_targets": (_i32, [_vp, _vp, _i64, _vp, ctypes.POINTER(cvx_integrate_params), _vp, _vp, _vp]),
+    "cvx_normalise_targets": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "cvx_profile_start": (_i32, [_i64]),
     "cvx_profile_stop": (_i32, []),
     "cvx_profile_read": (_i32, [_i32, _vp, _vp, _vp]),
@@ -214,6 +216,11 @@ def cvx_batch_error(batch: int) -> int:
 
 def cvx_batch_wave_limit(batch: int, max_scans_per_wave: int) -> None:
     check(lib().cvx_batch_wave_limit(batch, int(max_scans_per_wave)), "cvx_batch_wave_limit")
+
+
+def cvx_batch_test_missing_cta(batch: int, missing_cta: int, barrier_polls: int = 0) -> None:
+    check(lib().cvx_batch_test_missing_cta(batch, int(missing_cta), int(barrier_polls)),
+          "cvx_batch_test_missing_cta")
 
 
 def cvx_batch_timing(batch: int, enable: bool) -> None:
@@ -435,3 +442,12 @@ def cvx_training_targets(clean_handle: int, points, T_sub_sensor, params, e2_out
                                      _dev_ptr(e2_out, "torch.float32", "e2"),
                                      _dev_ptr(mask_out, "torch.float32", "mask"), _stream_handle(stream)),
           "cvx_training_targets")
+
+
+def cvx_normalise_targets(e2, mask, stream=None) -> float:
+    """Divide e2 (device float32 [n]) in place by its mean over mask; returns the mean."""
+    n = int(e2.shape[0])
+    out = ctypes.c_float(0.0)
+    check(lib().cvx_normalise_targets(_dev_ptr(e2, "torch.float32", "e2"), _dev_ptr(mask, "torch.float32", "mask"),
+                                      n, ctypes.byref(out), _stream_handle(stream)), "cvx_normalise_targets")
+    return float(out.value)

@@ -7,7 +7,7 @@
 //   phase 1  every tile of every scan of the wave: integrate_tile (count,
 //            allocate, per-voxel sums; Sec. III-D), tiles spread over all
 //            CTAs so uneven scans share the GPU (workload equalisation);
-//   phase 2  every touched block of every submap of the wave: merge_block;
+//   phase 2  every touched block of every submap of the wave: merge_span;
 //   phase 3  per-submap bookkeeping of the frame (counters, error words).
 // Phases are separated by grid barriers whose spins are bounded: a barrier
 // that gives up records CVX_ERR_TIMEOUT and every CTA leaves the kernel.
@@ -42,6 +42,8 @@ struct BatchDev {
   unsigned* bar_gen;
   int* err;
   unsigned long long* phase_ns;   // [n_waves * 3 + 1] globaltimer stamps, or nullptr
+  long long barrier_polls;        // polls before a grid barrier gives up
+  int missing_cta;                // test hook: this CTA leaves before its first arrival (-1: none)
 };
 
 __device__ __forceinline__ const SubmapDev& view(const BatchDev& b, int map, int wave) {
@@ -51,6 +53,19 @@ __device__ __forceinline__ const SubmapDev& view(const BatchDev& b, int map, int
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Sum of one value over the 256-thread CTA (thread 0 gets it).
+__device__ __forceinline__ unsigned long long cta_sum_b(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kTileThreads / 32; ++k) t += red[k];
+  __syncthreads();   // red is reused by the next call
   return t;
 }
 
@@ -75,7 +90,7 @@ __device__ bool grid_barrier(const BatchDev& b) {
     } else {
       long long it = 0;
       while (*((volatile unsigned*)b.bar_gen) == g) {
-        if (++it > kBarrierSpin || *((volatile int*)b.err) != 0) {
+        if (++it > b.barrier_polls || *((volatile int*)b.err) != 0) {
           atomicOr(b.err, kErrTimeout);
           ok = 0;
           break;
@@ -98,91 +113,70 @@ __device__ __forceinline__ int find_scan(const int* prefix, int lo, int hi, int 
   return lo;
 }
 
-// Merge work of wave w: every touched block of every submap of the wave,
-// taken in spans of kSpan consecutive blocks of the wave's concatenated
-// touched lists.  A span's pool indices, scans and skip flags are gathered in
-// one round of independent loads into shared memory; then each half CTA
-// merges pairs of blocks (loads of both in flight), so a block costs the
-// round trips of its sums and voxels only.  Spans first, first + step, ...
-// (single: only the first).
-constexpr int kSpan = 32;
+// Blocks a merge of wave w covers: the submap's allocated blocks -- with
+// pipelined waves as they stood when the wave's tiles had finished (the next
+// wave's tiles allocate meanwhile; every CTA must see the same count, since
+// the spans of all the wave's submaps are numbered together).
+__device__ __forceinline__ int wave_blocks(const BatchDev& b, const SubmapDev& m, int w) {
+  const int nb = b.pipelined ? *((volatile int32_t*)((w & 1) ? &m.st->nb_closed1 : &m.st->nb_closed0))
+                             : *((volatile int32_t*)&m.st->n_blocks);
+  return min(nb, m.max_blocks);
+}
 
-struct SpanSmem {
-  int pool[kSpan];
-  int scan[kSpan];
-  int skip[kSpan];
-};
-
-__device__ void merge_wave(const BatchDev& b, int w, const int* nt_prefix, int first, int step, bool single,
-                           SpanSmem* sp) {
-  const int tid = threadIdx.x;
+// Merge work of wave w: the allocated blocks of every submap of the wave in
+// spans of kSpanBlocks consecutive pool indices (a span never crosses
+// submaps; span_prefix counts them per scan of the wave).  In each span the
+// blocks stamped with the scan's epoch are compacted and merged (merge_span).
+// Spans first, first + step, ... (single: only the first).
+__device__ void merge_wave(const BatchDev& b, int w, const int* span_prefix, int first, int step, bool single,
+                           SpanList* sl, unsigned long long* red) {
   const int s0 = b.wave_begin[w], ns = b.wave_begin[w + 1] - s0;
-  const int nt_total = nt_prefix[ns];
-  const int half = tid >> 7, sub = tid & (kMergeThreads - 1);
-  for (int span = first;; span += step) {
-    const int g0 = span * kSpan;
-    if (g0 >= nt_total) break;
-    const int n = min(kSpan, nt_total - g0);
-    if (tid < n) {
-      const int q = find_scan(nt_prefix, 0, ns, g0 + tid);
-      const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
-      sp->pool[tid] = m.touched[g0 + tid - nt_prefix[q]];
-      sp->scan[tid] = q;
-      sp->skip[tid] = *((volatile int32_t*)m.frame_err) != 0;
+  const int total = span_prefix[ns];
+  for (int span = first; span < total; span += step) {
+    const int q = find_scan(span_prefix, 0, ns, span);
+    const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
+    const int nb = wave_blocks(b, m, w);
+    const int p0 = (span - span_prefix[q]) * kSpanBlocks;
+    const bool skip = *((volatile int32_t*)m.frame_err) != 0;
+    // the scan's epoch: its tiles ran with st->epoch + 1; pipelined waves have
+    // advanced st->epoch past them before their merges
+    const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + (b.pipelined ? 0u : 1u);
+    int t = 0;
+    const int merged = merge_span(m, p0, min(kSpanBlocks, nb - p0), ep, skip, sl, &t);
+    const unsigned long long c = cta_sum_b(merged, red);
+    if (threadIdx.x == 0) {
+      if (c) atomicAdd(&m.st->voxels_merged, c);
+      if (t) atomicAdd(&m.st->blocks_touched, (unsigned long long)t);
     }
-    __syncthreads();
-    for (int k = 2 * half; k < n; k += 4) {
-      const int q = sp->scan[k];
-      const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
-      const bool pair = k + 1 < n && sp->scan[k + 1] == q;   // a pair shares one submap
-      int merged = m.storage == 0 ? merge_pools<0>(m, sp->pool[k], pair ? sp->pool[k + 1] : -1, sp->skip[k], sub)
-                                  : merge_pools<1>(m, sp->pool[k], pair ? sp->pool[k + 1] : -1, sp->skip[k], sub);
-      unsigned long long c = merged;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if ((tid & 31) == 0 && c) atomicAdd(&m.st->voxels_merged, c);
-      if (!pair && k + 1 < n) {   // the next block starts the next submap
-        const SubmapDev& m2 = view(b, b.scan_map[s0 + sp->scan[k + 1]], w);
-        merged = m2.storage == 0 ? merge_pools<0>(m2, sp->pool[k + 1], -1, sp->skip[k + 1], sub)
-                                 : merge_pools<1>(m2, sp->pool[k + 1], -1, sp->skip[k + 1], sub);
-        c = merged;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if ((tid & 31) == 0 && c) atomicAdd(&m2.st->voxels_merged, c);
-      }
-    }
-    __syncthreads();   // the span's shared arrays are rewritten next
     if (single) break;
   }
 }
 
-// touched-block counts of wave w's scans (thread 0), prefix sums in nt_prefix
-__device__ void wave_touched(const BatchDev& b, int w, int* nt_prefix) {
+// spans of wave w's scans (thread 0), prefix sums in span_prefix
+__device__ void wave_spans(const BatchDev& b, int w, int* span_prefix) {
   if (threadIdx.x == 0) {
     const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
     int acc = 0;
     for (int s = s0; s < s1; ++s) {
-      nt_prefix[s - s0] = acc;
+      span_prefix[s - s0] = acc;
       const SubmapDev& m = view(b, b.scan_map[s], w);
-      acc += min(*((volatile int32_t*)m.n_touched), m.max_blocks);
+      acc += (wave_blocks(b, m, w) + kSpanBlocks - 1) / kSpanBlocks;
     }
-    nt_prefix[s1 - s0] = acc;
+    span_prefix[s1 - s0] = acc;
   }
   __syncthreads();
 }
 
 // per-submap bookkeeping of wave w's frames (CTA 0)
-__device__ void wave_bookkeeping(const BatchDev& b, int w, const int* nt_prefix) {
+__device__ void wave_bookkeeping(const BatchDev& b, int w) {
   if (blockIdx.x != 0) return;
   const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
   for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
     const SubmapDev& m = view(b, b.scan_map[s], w);
     State* st = m.st;
-    st->blocks_touched += (unsigned long long)(nt_prefix[s - s0 + 1] - nt_prefix[s - s0]);
     st->frames += 1;
     st->sticky_err |= *m.frame_err;
     *m.frame_err = 0;
-    *m.n_touched = 0;
     if (!b.pipelined) st->epoch += 1;   // the submap's next scan takes the next epoch
   }
 }
@@ -191,15 +185,21 @@ __device__ void wave_bookkeeping(const BatchDev& b, int w, const int* nt_prefix)
 // the next epoch (CTA 0, after the step's barrier)
 __device__ void wave_epoch(const BatchDev& b, int w) {
   if (blockIdx.x != 0) return;
-  for (int s = b.wave_begin[w] + threadIdx.x; s < b.wave_begin[w + 1]; s += blockDim.x)
-    view(b, b.scan_map[s], w).st->epoch += 1;
+  for (int s = b.wave_begin[w] + threadIdx.x; s < b.wave_begin[w + 1]; s += blockDim.x) {
+    State* st = view(b, b.scan_map[s], w).st;
+    if (w & 1) st->nb_closed1 = st->n_blocks;
+    else st->nb_closed0 = st->n_blocks;
+    st->epoch += 1;
+  }
 }
 
 template <int kVariant>
 __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ int nt_prefix[kMaxWaveScans + 1];
-  __shared__ SpanSmem span;
+  __shared__ int span_prefix[kMaxWaveScans + 1];
+  __shared__ SpanList span;
+  __shared__ unsigned long long red[kTileThreads / 32];
+  if ((int)blockIdx.x == b.missing_cta) return;   // test hook: never arrives at a barrier
   stamp(b, 0);
   if (!b.pipelined) {
     for (int w = 0; w < b.n_waves; ++w) {
@@ -214,12 +214,12 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
       if (!grid_barrier(b)) return;
       stamp(b, 3 * w + 1);
       // phase 2: merge every touched block of every submap of the wave
-      wave_touched(b, w, nt_prefix);
-      merge_wave(b, w, nt_prefix, blockIdx.x, gridDim.x, false, &span);
+      wave_spans(b, w, span_prefix);
+      merge_wave(b, w, span_prefix, blockIdx.x, gridDim.x, false, &span, red);
       if (!grid_barrier(b)) return;
       stamp(b, 3 * w + 2);
       // phase 3: per-submap bookkeeping of this frame
-      wave_bookkeeping(b, w, nt_prefix);
+      wave_bookkeeping(b, w);
       if (!grid_barrier(b)) return;
       stamp(b, 3 * w + 3);
     }
@@ -238,8 +238,8 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
     }
     int n_spans = 0;
     if (w > 0) {
-      wave_touched(b, w - 1, nt_prefix);
-      n_spans = (nt_prefix[b.wave_begin[w] - b.wave_begin[w - 1]] + kSpan - 1) / kSpan;   // merge spans
+      wave_spans(b, w - 1, span_prefix);
+      n_spans = span_prefix[b.wave_begin[w] - b.wave_begin[w - 1]];   // merge spans
     }
     const int items = n_tiles + n_spans;
     for (int it = blockIdx.x; it < items; it += gridDim.x) {
@@ -248,12 +248,12 @@ __global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
         integrate_tile_v<kVariant>(view(b, b.scan_map[s], w), b.scans[s], t0 + it - b.tile_prefix[s], smem,
                                    b.scan_lb[s]);
       } else {
-        merge_wave(b, w - 1, nt_prefix, it - n_tiles, 1, true, &span);   // one item: a span
+        merge_wave(b, w - 1, span_prefix, it - n_tiles, 1, true, &span, red);   // one item: a span
       }
     }
     if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 1);
-    if (w > 0) wave_bookkeeping(b, w - 1, nt_prefix);
+    if (w > 0) wave_bookkeeping(b, w - 1);
     if (w < b.n_waves) wave_epoch(b, w);
     if (!grid_barrier(b)) return;
     stamp(b, 3 * w + 2);
@@ -281,6 +281,8 @@ struct cvx_batch {
   bool timing;
   int last_waves;
   int wave_limit;     // most scans per wave (0: no limit)
+  int missing_cta;    // test hook (-1: off)
+  long long barrier_polls;
 };
 
 namespace {
@@ -335,6 +337,8 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
     return CVX_ERR_OOM;
   }
   b->lb_max = kMaxLocalBlocks;
+  b->missing_cta = -1;
+  b->barrier_polls = kBarrierSpin;
   if (cudaMalloc((void**)&b->phase_ns, sizeof(unsigned long long) * (3 * (size_t)max_scans + 8)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(b->dev);
@@ -372,6 +376,13 @@ void cvx_batch_destroy(cvx_batch* b) {
 cvx_status cvx_batch_wave_limit(cvx_batch* b, int32_t max_scans_per_wave) {
   if (!b || max_scans_per_wave < 0) return CVX_ERR_INVALID_ARG;
   b->wave_limit = max_scans_per_wave;
+  return CVX_OK;
+}
+
+cvx_status cvx_batch_test_missing_cta(cvx_batch* b, int32_t missing_cta, int64_t barrier_polls) {
+  if (!b) return CVX_ERR_INVALID_ARG;
+  b->missing_cta = missing_cta < 0 ? -1 : missing_cta;
+  b->barrier_polls = (missing_cta >= 0 && barrier_polls > 0) ? barrier_polls : kBarrierSpin;
   return CVX_OK;
 }
 
@@ -517,6 +528,8 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   bd.bar_gen = b->bar + 1;
   bd.err = (int*)(b->bar + 2);
   bd.phase_ns = b->timing ? b->phase_ns : nullptr;
+  bd.barrier_polls = b->barrier_polls;
+  bd.missing_cta = b->missing_cta;
   b->last_waves = pipelined ? n_waves + 1 : n_waves;   // pipelined: steps (tiles of w + merges of w - 1)
   if (cudaMemsetAsync(b->bar, 0, 16, st) != cudaSuccess) {
     cudaGetLastError();
@@ -525,7 +538,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   // one variant for every scan: a kernel holding only that code
   int variant = -2;
   for (int k = 0; k < n_run; ++k) {
-    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff, sd[order[k]].carve);
+    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff, sd[order[k]].carve || sd[order[k]].long_band);
     variant = variant == -2 ? v : (variant == v ? v : -1);
   }
   const BatchedFn kern = kBatched[variant + 1];

@@ -18,12 +18,12 @@ enum : int32_t { kErrCapacity = 1, kErrKeyRange = 2, kErrTimeout = 4 };
 // Device-resident bookkeeping of one submap.
 struct State {
   int32_t n_blocks;     // block pool bump pointer (allocation phase, Sec. III-D)
-  int32_t n_touched;    // distinct blocks of the current scan
-  int32_t frame_err;    // error bits of the current scan
-  int32_t sticky_err;   // OR of all scans' error bits
+  int32_t nb_closed0;   // batched pipelined waves: n_blocks when the tiles of the scan in
+  int32_t frame_err;    //   per-scan set 0 (nb_closed0) or 1 (nb_closed1) had finished
+  int32_t sticky_err;   // frame_err: error bits of the current scan; sticky_err: OR of all scans'
   uint32_t ticket;      // last-CTA detection of the merge pass
-  int32_t n_touched_b;  // second per-scan set of a pipelined submap
-  int32_t frame_err_b;
+  int32_t nb_closed1;
+  int32_t frame_err_b;  // second per-scan set of a pipelined submap
   int32_t parity;       // pipelined per-scan path: set the next scan accumulates into
   int32_t pending;      // pipelined per-scan path: set parity ^ 1 holds an unmerged scan
   uint32_t epoch;       // scans whose tiles have completed; the running scan's epoch is epoch + 1
@@ -34,21 +34,17 @@ struct State {
 struct SubmapDev {
   unsigned long long* keys;   // [slots] packed block keys, kEmptyKey when free
   int32_t* vals;              // [slots] pool index of the slot's block (-1: not yet published, -3: none)
-  uint32_t* epochs;           // [slots] epoch of the last scan that touched the slot's block, or
-                              // nullptr: per-scan touch map below instead
-  int32_t* touch;             // [max_blocks] per-scan touched mark (-1 when untouched), or nullptr
   int32_t* block_keys;        // [max_blocks,3] integer block coordinates
   void* D;                    // [max_blocks,512] float or half (D / trunc)
   void* W;                    // [max_blocks,512] float or half
   float2* acc;                // [max_blocks,512] per-scan sums (sum w (d - trunc), sum w), zero between scans
-  int32_t* touched;           // [max_blocks] pool index of each block touched by the scan
+  uint32_t* tepoch;           // [max_blocks] epoch of the last scan of this per-scan set that touched the
+                              // block: the scan's touched blocks are those holding its epoch
   State* st;
-  int32_t* n_touched;         // per-scan counters of this view (&st->n_touched or _b)
-  int32_t* frame_err;
+  int32_t* frame_err;         // error bits of this per-scan set (&st->frame_err or _b)
   uint32_t slot_mask;
   int32_t max_probe;
   int32_t max_blocks;
-  int32_t max_touched;
   float vs, inv_vs, trunc, max_w;
   int32_t storage;
 };
@@ -64,6 +60,7 @@ struct ScanDev {
   float min_range, max_range;
   int32_t weight_mode, dropoff, sensor, organised;
   int32_t carve;         // traverse from the sensor origin (free-space carving)
+  int32_t long_band;     // a band may cross more than 512 cells per axis (trunc > 250 voxels)
   int32_t height, width, tile_w, tile_h, tiles_x, n_tiles;
 };
 

@@ -5,13 +5,15 @@
 //   integrate_kernel : one CTA per tile of points; band traversal of every
 //                      point; blocks activated in the block hash through a
 //                      CTA-local cache (Sec. III-B "activate"), pool indices
-//                      claimed by atomic bump (allocation phase), the scan's
-//                      touched blocks compacted into a list; observation sums
-//                      reduced in shared memory and flushed with vector atomics
+//                      claimed by atomic bump (allocation phase), each touched
+//                      block stamped with the scan's epoch; observation sums
+//                      reduced in shared memory or by L2 vector reductions
 //                      (segmented reduction of commutative sums).
-//   merge_kernel     : one CTA per touched block: merge into D and W with
-//                      coalesced vector loads and stores; the last CTA resets
-//                      the per-scan state.  One owner per block: no write races.
+//   merge_kernel     : spans of 32 allocated blocks per CTA: the blocks stamped
+//                      with the scan's epoch (the stream compaction) merged
+//                      into D and W with coalesced vector loads and stores;
+//                      the last CTA closes the frame.  One owner per block: no
+//                      write races.
 // A submap created with CVX_SUBMAP_PIPELINED runs one kernel per scan
 // instead (integrate_pipelined_kernel): the merges of the previous scan share
 // the launch with this scan's tiles, and flush_kernel merges the last scan
@@ -48,56 +50,75 @@ const IntegrateFn kIntegrate[7] = {integrate_kernel<-1>, integrate_kernel<0>, in
                                    integrate_kernel<2>,  integrate_kernel<3>, integrate_kernel<4>,
                                    integrate_kernel<5>};   // [variant + 1]
 
-template <int kStore>
-__global__ void __launch_bounds__(kMergeThreads) merge_kernel(SubmapDev m) {
-  __shared__ int head[2];
-  __shared__ unsigned long long red[kMergeThreads / 32];
-  // The first pair's pool indices, read before the scan's block count is
-  // known (entries past it are stale but in bounds and unused): their round
-  // trip overlaps the one of the count.
-  const int g = (int)gridDim.x;
-  const int j_first = blockIdx.x;
-  const int p_first0 = j_first < m.max_blocks ? m.touched[j_first] : -1;
-  const int p_first1 = j_first + g < m.max_blocks ? m.touched[j_first + g] : -1;
+// Sum of one value over a 256-thread CTA (thread 0 gets it).
+__device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsigned long long* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kTileThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+// Merge of one scan: every allocated block's touch epoch checked, span by
+// span.  Reads, by thread 0, the scan's block count, error bits and epoch, then
+// takes a ticket (the fence orders the reads first; nothing is in flight
+// yet).  The CTA drawing the last ticket knows every CTA has read them and
+// closes the frame at once; the others merge from the values they read.
+__global__ void __launch_bounds__(kTileThreads) merge_kernel(SubmapDev m) {
+  __shared__ int head[3];
+  __shared__ SpanList sl;
+  __shared__ unsigned long long red[kTileThreads / 32];
   if (threadIdx.x == 0) {
-    // Read the scan's touched-block count and error bits, then take a ticket
-    // (the fence orders the reads first; nothing is in flight yet).  The CTA
-    // drawing the last ticket knows every CTA has read them and closes the
-    // frame at once; the others merge from the values they read.
-    const int nt = min(*((volatile int32_t*)m.n_touched), m.max_blocks);
+    const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
     const int fe = *((volatile int32_t*)m.frame_err);
-    head[0] = nt;
+    const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u;
+    head[0] = nb;
     head[1] = fe;
+    head[2] = (int)ep;
     __threadfence();
     if (atomicAdd(&m.st->ticket, 1u) == gridDim.x - 1) {
       State* st = m.st;
-      st->blocks_touched += (unsigned long long)nt;
       st->frames += 1;
       st->sticky_err |= fe;
       st->epoch += 1;   // the next scan's tiles take the next epoch
       *m.frame_err = 0;
-      *m.n_touched = 0;
       st->ticket = 0;
     }
   }
   __syncthreads();
-  const int nt = head[0];
+  const int nb = head[0];
   const bool skip = head[1] != 0;
-  const int tid = threadIdx.x;
-  unsigned long long merged = 0;
-  if (j_first < nt) merged += merge_pools<kStore>(m, p_first0, j_first + g < nt ? p_first1 : -1, skip, tid);
-  for (int j = j_first + 2 * g; j < nt; j += 2 * g) {
-    const int j1 = j + g < nt ? j + g : -1;
-    merged += merge_two<kStore>(m, j, j1, skip, tid);
+  const uint32_t ep = (uint32_t)head[2];
+  unsigned long long merged = 0, touched = 0;
+  for (int p0 = blockIdx.x * kSpanBlocks; p0 < nb; p0 += gridDim.x * kSpanBlocks) {
+    int t = 0;
+    merged += merge_span(m, p0, min(kSpanBlocks, nb - p0), ep, skip, &sl, &t);
+    touched += t;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) merged += __shfl_xor_sync(0xffffffffu, merged, o);
-  if ((tid & 31) == 0) red[tid >> 5] = merged;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long t = 0;
-    for (int w = 0; w < kMergeThreads / 32; ++w) t += red[w];
-    if (t) atomicAdd(&m.st->voxels_merged, t);
+  const unsigned long long sum = cta_sum(merged, red);
+  if (threadIdx.x == 0) {
+    if (sum) atomicAdd(&m.st->voxels_merged, sum);
+    if (touched) atomicAdd(&m.st->blocks_touched, touched);
+  }
+}
+
+// Clear the per-scan sums a launch that gave up left unmerged: the blocks of
+// either per-scan set stamped with the last or the running scan's epoch
+// (reset; merged blocks hold zero sums, so this only repeats their zeroing).
+__global__ void discard_sums_kernel(SubmapDev a, SubmapDev b, int two_sets) {
+  const int nb = min(a.st->n_blocks, a.max_blocks);
+  const uint32_t e = a.st->epoch;
+  for (int set = 0; set <= two_sets; ++set) {
+    const SubmapDev& m = set ? b : a;
+    for (int p = blockIdx.x; p < nb; p += gridDim.x) {
+      const uint32_t t = m.tepoch[p];
+      if (t != e && t != e + 1u) continue;
+      float4* acc = reinterpret_cast<float4*>(m.acc + (size_t)p * kVoxPerBlock);
+      for (int q = threadIdx.x; q < kVoxPerBlock / 2; q += blockDim.x) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
 }
 
@@ -114,44 +135,33 @@ __global__ void zero_pool_kernel(SubmapDev m, int bytes_per_block) {
 
 // The per-scan set `which` of a pipelined submap: a describes set 0 (and
 // everything the sets share), b the second set (a copy of a but for acc,
-// touch, touched, n_touched and frame_err).
+// tepoch and frame_err).
 __device__ __forceinline__ SubmapDev pick_set(const SubmapDev& a, const SubmapDev& b, int which) {
   SubmapDev m = a;
   if (which) {
     m.acc = b.acc;
-    m.touch = b.touch;
-    m.touched = b.touched;
-    m.n_touched = b.n_touched;
+    m.tepoch = b.tepoch;
     m.frame_err = b.frame_err;
   }
   return m;
 }
 
-// Merge the first nt touched blocks of set m: items first, first + step, ...
-// of four consecutive blocks per 256-thread CTA (a pair per half CTA, loads of
-// both in flight).  Returns the voxels this thread merged.
-__device__ __noinline__ int merge_set(const SubmapDev& m, int nt, bool skip, int first, int step, int tid) {
-  const int half = tid / kMergeThreads, sub = tid % kMergeThreads;
-  int merged = 0;
-  for (int item = first;; item += step) {
-    const int j = 4 * item + 2 * half;
-    if (j >= nt) break;
-    const int j1 = j + 1 < nt ? j + 1 : -1;
-    merged += m.storage == CVX_STORE_F32 ? merge_two<0>(m, j, j1, skip, sub) : merge_two<1>(m, j, j1, skip, sub);
+// Merge the blocks of set m stamped with epoch ep among the first nb pool
+// indices: spans first, first + step, ... (256-thread CTA).  Adds the merged
+// voxels and touched blocks to the submap's counters.
+__device__ __noinline__ void merge_set(const SubmapDev& m, int nb, uint32_t ep, bool skip, int first, int step,
+                                       SpanList* sl, unsigned long long* red) {
+  unsigned long long merged = 0, touched = 0;
+  for (int span = first; span * kSpanBlocks < nb; span += step) {
+    int t = 0;
+    merged += merge_span(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl, &t);
+    touched += t;
   }
-  return merged;
-}
-
-// Sum of one value over a 256-thread CTA (thread 0 gets it).
-__device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsigned long long* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  unsigned long long t = 0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < kTileThreads / 32; ++w) t += red[w];
-  return t;
+  const unsigned long long sum = cta_sum(merged, red);
+  if (threadIdx.x == 0) {
+    if (sum) atomicAdd(&m.st->voxels_merged, sum);
+    if (touched) atomicAdd(&m.st->blocks_touched, touched);
+  }
 }
 
 // Per-scan words of a pipelined submap as one launch sees them.  Thread 0 of
@@ -164,8 +174,9 @@ __device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsi
 struct PipeHead {
   int par;       // set this launch accumulates into
   int pending;   // set par ^ 1 holds a scan to merge
-  int nt;        // its touched blocks
-  int fe;        // its error bits
+  int nb;        // allocated blocks
+  int fe;        // the pending scan's error bits
+  uint32_t ep;   // its epoch
 };
 
 __device__ __forceinline__ void pipe_head(const SubmapDev& a, const SubmapDev& b, int pend_after, bool flip,
@@ -174,22 +185,18 @@ __device__ __forceinline__ void pipe_head(const SubmapDev& a, const SubmapDev& b
     State* st = a.st;
     const int par = *((volatile int32_t*)&st->parity);
     const int pend = *((volatile int32_t*)&st->pending);
-    int32_t* ntp = par ? a.n_touched : b.n_touched;   // the pending set is par ^ 1
-    int32_t* fep = par ? a.frame_err : b.frame_err;
-    const int nt = pend ? min(*((volatile int32_t*)ntp), a.max_blocks) : 0;
-    const int fe = pend ? *((volatile int32_t*)fep) : 0;
+    int32_t* fep = par ? a.frame_err : b.frame_err;   // the pending set is par ^ 1
     h->par = par;
     h->pending = pend;
-    h->nt = nt;
-    h->fe = fe;
+    h->nb = min(*((volatile int32_t*)&st->n_blocks), a.max_blocks);
+    h->fe = pend ? *((volatile int32_t*)fep) : 0;
+    h->ep = *((volatile uint32_t*)&st->epoch);        // the pending scan closed its tiles with this epoch
     __threadfence();
     if (atomicAdd(&st->ticket, 1u) == gridDim.x - 1) {
       if (pend) {
-        st->blocks_touched += (unsigned long long)nt;
         st->frames += 1;
-        st->sticky_err |= fe;
+        st->sticky_err |= h->fe;
         *fep = 0;
-        *ntp = 0;
       }
       st->pending = pend_after;
       if (flip) st->parity = par ^ 1;
@@ -212,6 +219,7 @@ __global__ void __launch_bounds__(kTileThreads, 5) integrate_pipelined_kernel(Su
                                                                            int lb, int n_merge) {
   extern __shared__ __align__(16) char smem[];
   __shared__ unsigned long long red[kTileThreads / 32];
+  __shared__ SpanList sl;
   const int par = *((volatile int32_t*)&a.st->parity);
   if ((int)blockIdx.x < sc.n_tiles) {
     integrate_tile_v<kVariant>(pick_set(a, b, par), sc, (int)blockIdx.x, smem, lb);
@@ -219,11 +227,11 @@ __global__ void __launch_bounds__(kTileThreads, 5) integrate_pipelined_kernel(Su
   }
   if (*((volatile int32_t*)&a.st->pending) == 0) return;   // uniform over the merging CTAs
   const SubmapDev prev = pick_set(a, b, par ^ 1);
-  const int nt = min(*((volatile int32_t*)prev.n_touched), prev.max_blocks);
+  // blocks this scan's tiles allocate meanwhile carry other epochs: any count read here will do
+  const int nb = min(*((volatile int32_t*)&a.st->n_blocks), a.max_blocks);
   const bool skip = *((volatile int32_t*)prev.frame_err) != 0;
-  const int merged = merge_set(prev, nt, skip, (int)blockIdx.x - sc.n_tiles, n_merge, threadIdx.x);
-  const unsigned long long t = cta_sum((unsigned long long)merged, red);
-  if (threadIdx.x == 0 && t) atomicAdd(&a.st->voxels_merged, t);
+  const uint32_t ep = *((volatile uint32_t*)&a.st->epoch);   // the previous scan's epoch
+  merge_set(prev, nb, ep, skip, (int)blockIdx.x - sc.n_tiles, n_merge, &sl, red);
 }
 
 // One thread, after integrate_pipelined_kernel: close the frame it merged
@@ -233,13 +241,10 @@ __global__ void pipe_close_kernel(SubmapDev a, SubmapDev b) {
   State* st = a.st;
   const int par = st->parity;
   if (st->pending) {
-    int32_t* ntp = par ? a.n_touched : b.n_touched;   // the pending set is par ^ 1
-    int32_t* fep = par ? a.frame_err : b.frame_err;
-    st->blocks_touched += (unsigned long long)min(*ntp, a.max_blocks);
+    int32_t* fep = par ? a.frame_err : b.frame_err;   // the pending set is par ^ 1
     st->frames += 1;
     st->sticky_err |= *fep;
     *fep = 0;
-    *ntp = 0;
   }
   st->pending = 1;
   st->parity = par ^ 1;
@@ -257,12 +262,10 @@ const PipelinedFn kPipelined[7] = {integrate_pipelined_kernel<-1>, integrate_pip
 __global__ void __launch_bounds__(kTileThreads) flush_kernel(SubmapDev a, SubmapDev b, int discard) {
   __shared__ PipeHead h;
   __shared__ unsigned long long red[kTileThreads / 32];
+  __shared__ SpanList sl;
   pipe_head(a, b, 0, false, &h);
   if (!h.pending) return;   // uniform over the grid
-  const int merged =
-      merge_set(pick_set(a, b, h.par ^ 1), h.nt, discard || h.fe != 0, blockIdx.x, gridDim.x, threadIdx.x);
-  const unsigned long long t = cta_sum((unsigned long long)merged, red);
-  if (threadIdx.x == 0 && t) atomicAdd(&a.st->voxels_merged, t);
+  merge_set(pick_set(a, b, h.par ^ 1), h.nb, h.ep, discard || h.fe != 0, blockIdx.x, gridDim.x, &sl, red);
 }
 
 }  // namespace
@@ -365,21 +368,19 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   SubmapDev& d = m->dev;
   d.keys = (unsigned long long*)sub_alloc(m, slots * 8);
   d.vals = (int32_t*)sub_alloc(m, slots * 4);
-  d.epochs = (uint32_t*)sub_alloc(m, slots * 4);
-  d.touch = nullptr;   // scan epochs in the slots mark touched blocks
   d.block_keys = (int32_t*)sub_alloc(m, nb * 12);
   d.D = sub_alloc(m, nb * kVoxPerBlock * m->bytes_per_vox);
   d.W = sub_alloc(m, nb * kVoxPerBlock * m->bytes_per_vox);
   d.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
-  d.touched = (int32_t*)sub_alloc(m, nb * 4);
+  d.tepoch = (uint32_t*)sub_alloc(m, nb * 4);
   d.st = (State*)sub_alloc(m, sizeof(State));
-  int expect = 9;
+  int expect = 8;
   m->pipelined = (p->flags & CVX_SUBMAP_PIPELINED) != 0;
   SubmapDev& db = m->dev_b;
-  if (m->pipelined) {   // second per-scan set: sums and touched list
+  if (m->pipelined) {   // second per-scan set: sums and touch epochs
     db.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
-    db.touched = (int32_t*)sub_alloc(m, nb * 4);
-    expect = 11;
+    db.tepoch = (uint32_t*)sub_alloc(m, nb * 4);
+    expect = 10;
   }
   if (m->n_allocs != expect) {
     sub_free_all(m);
@@ -389,9 +390,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.slot_mask = (uint32_t)(slots - 1);
   d.max_probe = (int)std::min<size_t>(slots, 4096);
   d.max_blocks = (int)nb;
-  d.max_touched = (int)nb;
   d.storage = p->storage;
-  d.n_touched = &d.st->n_touched;
   d.frame_err = &d.st->frame_err;
   d.vs = p->voxel_size;
   d.inv_vs = 1.0f / p->voxel_size;
@@ -399,24 +398,24 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.max_w = p->max_weight;
   if (m->pipelined) {
     float2* acc_b = db.acc;
-    int32_t* touched_b = db.touched;
+    uint32_t* tepoch_b = db.tepoch;
     db = d;
     db.acc = acc_b;
-    db.touched = touched_b;
-    db.n_touched = &d.st->n_touched_b;
+    db.tepoch = tepoch_b;
     db.frame_err = &d.st->frame_err_b;
   }
   cudaStream_t s = (cudaStream_t)p->stream;
   m->last_stream = s;
   cudaMemsetAsync(d.keys, 0xff, slots * 8, s);
   cudaMemsetAsync(d.vals, 0xff, slots * 4, s);
-  cudaMemsetAsync(d.epochs, 0, slots * 4, s);
+  cudaMemsetAsync(d.tepoch, 0, nb * 4, s);
   cudaMemsetAsync(d.D, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.W, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
   cudaMemsetAsync(d.st, 0, sizeof(State), s);
   if (m->pipelined) {
     cudaMemsetAsync(db.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
+    cudaMemsetAsync(db.tepoch, 0, nb * 4, s);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
@@ -442,7 +441,7 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
   if (kernel_attributes() != CVX_OK) return CVX_ERR_CUDA;
   if (map->pipelined) {
     const int n_merge = num_sms();
-    const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff, sc.carve) + 1];
+    const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff, sc.carve || sc.long_band) + 1];
     COVOX_LAUNCH(kKPipelined, s,
                  pf<<<n_merge + sc.n_tiles, kTileThreads, smem, s>>>(map->dev, map->dev_b, sc, lb, n_merge));
     COVOX_LAUNCH(kKPipeClose, s, pipe_close_kernel<<<1, 1, 0, s>>>(map->dev, map->dev_b));
@@ -450,13 +449,10 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
     map->maybe_pending = true;
     return CVX_OK;
   }
-  const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff, sc.carve) + 1];
+  const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff, sc.carve || sc.long_band) + 1];
   COVOX_LAUNCH(kKAccum, s, fn<<<sc.n_tiles, kTileThreads, smem, s>>>(map->dev, sc, lb));
-  const int grid = std::min<int>(map->dev.max_blocks, num_sms() * 2);
-  if (map->p.storage == CVX_STORE_F32)
-    COVOX_LAUNCH(kKMerge, s, merge_kernel<0><<<grid, kMergeThreads, 0, s>>>(map->dev));
-  else
-    COVOX_LAUNCH(kKMerge, s, merge_kernel<1><<<grid, kMergeThreads, 0, s>>>(map->dev));
+  const int grid = std::min<int>((map->dev.max_blocks + kSpanBlocks - 1) / kSpanBlocks, num_sms() * 2);
+  COVOX_LAUNCH(kKMerge, s, merge_kernel<<<grid, kTileThreads, 0, s>>>(map->dev));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
 
@@ -497,10 +493,14 @@ cvx_status cvx_reset_submap(cvx_submap* map, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   map->last_stream = s;
   if (flush_pending(map, s, true) != CVX_OK) return CVX_ERR_CUDA;
+  COVOX_LAUNCH(kKDiscard, s,
+               discard_sums_kernel<<<num_sms(), 256, 0, s>>>(map->dev, map->dev_b, map->pipelined ? 1 : 0));
   const int bpb = (int)(kVoxPerBlock * map->bytes_per_vox);
   COVOX_LAUNCH(kKZeroPool, s, zero_pool_kernel<<<num_sms() * 4, 256, 0, s>>>(map->dev, bpb));
   cudaMemsetAsync(map->dev.keys, 0xff, (size_t)map->p.hash_slots * 8, s);
   cudaMemsetAsync(map->dev.vals, 0xff, (size_t)map->p.hash_slots * 4, s);
+  cudaMemsetAsync(map->dev.tepoch, 0, (size_t)map->p.max_blocks * 4, s);
+  if (map->pipelined) cudaMemsetAsync(map->dev_b.tepoch, 0, (size_t)map->p.max_blocks * 4, s);
   cudaMemsetAsync(map->dev.st, 0, sizeof(State), s);
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }

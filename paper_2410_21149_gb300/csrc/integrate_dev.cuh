@@ -6,9 +6,12 @@
 //                    per-voxel sums of the tile's blocks in shared memory,
 //                    then one activation per distinct block (Sec. III-B) and a
 //                    vector-atomic flush into the blocks' per-scan sums.
-//   merge_block    : one touched block: D <- (D W + sum w d)/(W + sum w),
-//                    W <- min(W + sum w, max_weight) for voxels with sum w > 0,
-//                    with vectorised loads/stores; clears the accumulator.
+//   merge_span     : the blocks of a span of pool indices that the scan
+//                    touched (their touch epoch is the scan's: the stream
+//                    compaction of the allocation pass, Sec. III-D), each
+//                    D <- (D W + sum w d)/(W + sum w), W <- min(W + sum w,
+//                    max_weight) for voxels with sum w > 0, with vectorised
+//                    loads/stores; clears the sums.
 #pragma once
 
 #include "covox_dev.cuh"
@@ -18,41 +21,28 @@ namespace covox {
 constexpr int kTileThreads = 256;
 constexpr int kTileBlocks = 64;      // distinct blocks recorded per tile (power of two)
 constexpr int kMapDead = -3;         // vals[] marker: block unusable (pool exhausted)
-constexpr long long kSpinLimit = 1 << 22;
-
-// The scan's entry in its touched list (one per block and scan).
-__device__ __forceinline__ void append_touched(const SubmapDev& m, int pool) {
-  const int j = atomicAdd(m.n_touched, 1);   // j < max_blocks: each block once per scan
-  m.touched[j] = pool;
-}
-
-// First activation of a block in this scan: touch map variant (no epochs).
-__device__ __forceinline__ void touch_block(const SubmapDev& m, int pool) {
-  if (*((volatile int32_t*)(m.touch + pool)) == -1 && atomicCAS(m.touch + pool, -1, -2) == -1)
-    append_touched(m, pool);
-}
+constexpr long long kSpinLimit = 1 << 20;   // polls of an unpublished slot (~1 s)
 
 // Global activation of one block ("activate", Sec. III-B: insert-or-find,
-// pool index by atomic bump for a new block, entry in the scan's touched
-// list).  Returns the pool index or -1 (error recorded).
+// pool index by atomic bump for a new block), and its mark as touched by the
+// scan: the block's touch epoch is set to the scan's epoch `ep` (a plain
+// store; every toucher writes the same value).  Returns the pool index or -1
+// (error recorded).
 //
-// A slot holds the packed key, the pool index and (when m.epochs is set) the
-// epoch of the last scan that touched the block.  The probe loads all three
-// of a slot at once -- their addresses do not depend on each other -- so a
-// block that this scan has already activated costs one round trip.  The
-// first toucher of a scan is the thread whose CAS moves the slot's epoch to
-// `ep`; the inserter of a new block sets the epoch before it publishes the
-// pool index, so a thread that read a stale epoch fails its CAS.
+// A slot holds the packed key and the pool index; the probe loads both at
+// once, so finding an existing block costs one L2 round trip and nothing
+// waits on an atomic.  The inserter of a new block publishes its pool index
+// after writing the block's key; a thread that finds the key before that
+// waits for the publication (bounded).
 __device__ inline int global_activate(const SubmapDev& m, unsigned long long key, uint32_t ep) {
   uint32_t s = hash_key(key) & m.slot_mask;
   for (int p = 0; p < m.max_probe; ++p) {
     const unsigned long long cur = *((volatile unsigned long long*)(m.keys + s));
     int pool = *((volatile int32_t*)(m.vals + s));
-    uint32_t e = m.epochs ? *((volatile uint32_t*)(m.epochs + s)) : 0u;
     bool found = cur == key;
     if (cur == kEmptyKey) {
       const unsigned long long old = atomicCAS(m.keys + s, kEmptyKey, key);
-      if (old == kEmptyKey) {   // inserted: allocate, publish, first toucher
+      if (old == kEmptyKey) {   // inserted: allocate, publish
         pool = atomicAdd(&m.st->n_blocks, 1);
         if (pool >= m.max_blocks) {
           atomicOr(m.frame_err, kErrCapacity);
@@ -62,13 +52,8 @@ __device__ inline int global_activate(const SubmapDev& m, unsigned long long key
         m.block_keys[3 * pool] = (int)((key >> 42) & 0x1fffff) - (1 << 20);
         m.block_keys[3 * pool + 1] = (int)((key >> 21) & 0x1fffff) - (1 << 20);
         m.block_keys[3 * pool + 2] = (int)(key & 0x1fffff) - (1 << 20);
-        if (m.epochs) {
-          m.epochs[s] = ep;
-          __threadfence();
-        }
+        m.tepoch[pool] = ep;
         atomicExch(m.vals + s, pool);   // publish
-        if (m.epochs) append_touched(m, pool);
-        else touch_block(m, pool);
         return pool;
       }
       found = old == key;
@@ -78,18 +63,13 @@ __device__ inline int global_activate(const SubmapDev& m, unsigned long long key
       for (long long it = 0; pool == -1 && it < kSpinLimit; ++it) {   // the inserter publishes shortly
         __nanosleep(64);
         pool = *((volatile int32_t*)(m.vals + s));
-        if (m.epochs) e = *((volatile uint32_t*)(m.epochs + s));
       }
       if (pool == -1) {
         atomicOr(m.frame_err, kErrTimeout);
         return -1;
       }
       if (pool < 0) return -1;   // block unusable (pool was exhausted)
-      if (m.epochs) {
-        if (e != ep && atomicCAS(m.epochs + s, e, ep) == e) append_touched(m, pool);
-      } else {
-        touch_block(m, pool);
-      }
+      m.tepoch[pool] = ep;
       return pool;
     }
     s = (s + 1) & m.slot_mask;
@@ -168,8 +148,8 @@ __device__ __forceinline__ int tile_iters(const ScanDev& sc) {
 // single CAS, so lookups never wait.  Observations add w*d and w to the slot
 // with shared atomics.  After the pass the tile's distinct blocks (its count
 // phase) are activated once each in the block hash (Sec. III-B "activate":
-// insert-or-find, pool index by atomic bump, entry in the scan's touched list:
-// Sec. III-D allocation phase) and the slots are flushed with vector atomics
+// insert-or-find, pool index by atomic bump, touch epoch: Sec. III-D
+// allocation phase) and the slots are flushed with vector atomics
 // into the blocks' per-scan accumulators.  A block that finds the map full is
 // activated on the spot and accumulated straight into global memory.
 __device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
@@ -200,11 +180,16 @@ struct TileSmem {
   unsigned long long* red;    // [2 * warps]
   unsigned long long* ckey;   // [kCache] block -> pool cache
   int* cpool;                 // [kCache]
+  int* list;                  // [warps * kListPerWarp] each warp's compacted candidate points
 };
+
+constexpr int kGather = 8;                  // tile iterations gathered per compaction round
+constexpr int kListPerWarp = kGather * 32;
 
 __host__ __device__ inline size_t tile_smem_bytes(int lb) {
   return (size_t)lb * 8 + (size_t)lb * 4 + 2 * (kTileThreads / 32) * 8 + 16 + (size_t)lb * kVoxPerBlock * 16 +
-         (size_t)kCache * 12 + 16 + (kTileThreads / 32) * 4 + 16;
+         (size_t)kCache * 12 + 16 + (kTileThreads / 32) * 4 + 16 + (size_t)(kTileThreads / 32) * kListPerWarp * 4 +
+         16;
 }
 
 __device__ inline TileSmem tile_smem(char* base, int lb) {
@@ -228,6 +213,8 @@ __device__ inline TileSmem tile_smem(char* base, int lb) {
   t.wmax = reinterpret_cast<float*>(base);
   base += ((kTileThreads / 32) * 4 + 15) / 16 * 16;
   t.pool = reinterpret_cast<int*>(base);
+  base += ((size_t)lb * 4 + 15) / 16 * 16;
+  t.list = reinterpret_cast<int*>(base);
   return t;
 }
 
@@ -318,8 +305,13 @@ __device__ __forceinline__ int local_slot(const TileSmem& t, int lb, unsigned lo
   return -1;
 }
 
+// The general form of the tile phase, one point after another per thread:
+// any band length, and free-space carving (rays from the sensor origin, with
+// the distance recomputed exactly near the band).  Scans without carving and
+// with bands of at most 512 cells per axis take integrate_tile_t below.
 template <bool kLocal, int kDrop, bool kCarve = false>
-__device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+__device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& sc, int tile, char* smem,
+                                             int lb) {
   const TileSmem t = tile_smem(smem, lb);
   const int tid = threadIdx.x;
   for (int q = tid; q < kCache; q += kTileThreads) {
@@ -328,7 +320,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
   }
   const TilePoints tp(sc, tile);
   const int iters = tile_iters(sc);
-  const uint32_t ep = m.epochs ? *((volatile uint32_t*)&m.st->epoch) + 1u : 0u;   // this scan's epoch
+  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u;   // this scan's epoch
   Fixed fx;
   if (kLocal) {
     for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
@@ -496,6 +488,312 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
   __syncthreads();   // shared memory is reused by the caller's next tile
 }
 
+// ------------------------------------------------- tile phase, warp-parallel
+// A point survives the first test if its coordinates are finite, it lies in
+// front of a pinhole sensor and its per-point weight (if any) is usable; the
+// range gate, which needs the transformed ray, is make_ray's.
+__device__ __forceinline__ bool point_candidate(const ScanDev& sc, long long i) {
+  const float x = __ldg(sc.pts + 3 * i), y = __ldg(sc.pts + 3 * i + 1), z = __ldg(sc.pts + 3 * i + 2);
+  if (!(isfinite(x) && isfinite(y) && isfinite(z))) return false;
+  if (sc.sensor == 0 && !(z > 0.0f)) return false;
+  if (sc.weight_mode == 2) {
+    const float w = __ldg(sc.pw + i);
+    if (!(isfinite(w) && w >= 0.0f)) return false;
+  }
+  return true;
+}
+
+// Band traversal state of one ray.  The tMax of an axis that has reached its
+// end cell is +inf, so the axis to step is the plain argmin of the three tMax
+// values with ties to the lowest axis: the rule of Dda::step (an axis with no
+// crossing left can never be chosen, and an axis with crossings left never
+// holds +inf: one whose 1/|B - A| overflowed holds the largest finite float).
+// Per axis two counters sit in 10-bit fields of two words: the steps left on
+// the axis, biased by 511 (the axis reaches its end cell when bit 9 of its
+// field clears), and the steps left before the next block boundary, biased by
+// 8 (the step crosses into the neighbouring block when bit 3 clears).  One
+// subtraction steps the chosen axis in both words.
+struct Walk {
+  float tm0, tm1, tm2, td0, td1, td2;
+  float dist, dd0, dd1, dd2;   // distance of the current cell; change per step on each axis
+  int dl0, dl1, dl2;           // change of the local voxel index per step on each axis
+  uint32_t nrem, cb;
+  int l, left;
+};
+
+// The same initial values as Dda::init (operation for operation), then the
+// packed counters.  v and e receive the start and end cells.  False if an
+// axis needs more than 512 steps (not representable: the host sends such
+// scans to integrate_tile_legacy).
+__device__ __forceinline__ bool walk_init(const Ray& r, const float A[3], const float B[3], float vs, Walk& w,
+                                          int v[3], int e[3]) {
+  float tm[3], td[3];
+  int s[3];
+  w.left = 0;
+  w.nrem = 0;
+  w.cb = 0;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    v[k] = (int)floorf(A[k]);
+    e[k] = (int)floorf(B[k]);
+    const float d = __fsub_rn(B[k], A[k]);
+    if (d > 0.0f) {
+      s[k] = 1;
+      td[k] = __frcp_rn(d);
+      tm[k] = __fmul_rn(__fsub_rn((float)(v[k] + 1), A[k]), td[k]);
+    } else if (d < 0.0f) {
+      s[k] = -1;
+      td[k] = __frcp_rn(-d);
+      tm[k] = __fmul_rn(__fsub_rn(A[k], (float)v[k]), td[k]);
+    } else {
+      s[k] = 0;
+      td[k] = __int_as_float(0x7f800000);
+      tm[k] = __int_as_float(0x7f800000);
+    }
+    const int n = abs(e[k] - v[k]);
+    w.left += n;
+    ok = ok && n <= 512;
+    if (n == 0) tm[k] = __int_as_float(0x7f800000);
+    else if (isinf(tm[k])) tm[k] = 3.40282347e38f;
+    const int c = v[k] & 7;
+    w.nrem |= (uint32_t)(min(n, 512) + 511) << (10 * k);
+    w.cb |= (uint32_t)((s[k] > 0 ? 7 - c : (s[k] < 0 ? c : 7)) + 8) << (10 * k);
+  }
+  w.tm0 = tm[0]; w.tm1 = tm[1]; w.tm2 = tm[2];
+  w.td0 = td[0]; w.td1 = td[1]; w.td2 = td[2];
+  w.dl0 = s[0]; w.dl1 = 8 * s[1]; w.dl2 = 64 * s[2];
+  w.dist = voxel_distance_raw(r, v, vs);
+  w.dd0 = -(float)s[0] * vs * r.u[0];
+  w.dd1 = -(float)s[1] * vs * r.u[1];
+  w.dd2 = -(float)s[2] * vs * r.u[2];
+  w.l = local_index(v);
+  return ok;
+}
+
+// Shared slot and pool index of the block `key` for the lanes of the warp in
+// `act` (this lane takes part if `on`): lanes holding the same key elect the
+// lowest as leader, which looks it up (shared slot, CTA cache, global hash);
+// the others read the answer from it.  Lanes outside `act` return at once and
+// keep their outputs.
+template <bool kLocal>
+__device__ __forceinline__ void warp_lookup(const SubmapDev& m, const TileSmem& t, int lb, uint32_t ep,
+                                            unsigned act, bool on, unsigned long long key, int& slot, int& pool) {
+  if (!on) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(act, key);
+  const int leader = __ffs(peers) - 1;
+  int s = -1, p = -1;
+  if (lane == leader) {
+    s = kLocal ? local_slot(t, lb, key) : -1;
+    if (s < 0) p = cached_pool(m, t, key, ep);
+  }
+  if (kLocal) s = __shfl_sync(act, s, leader);
+  p = __shfl_sync(act, p, leader);
+  slot = s;
+  pool = p;
+}
+
+// Count + allocate + process for one tile (coVoxSLAM Sec. III-D), warp by
+// warp.  Each warp first gathers its valid points (a ballot per iteration,
+// so invalid points -- no return, out of range -- leave no idle lanes in the
+// traversal), then takes them 32 at a time: ray set-up, one warp-aggregated
+// lookup of each band's first and last block (Sec. III-B "activate"), and the band
+// traversal with one observation per cell: w (d - trunc) and w added to the
+// block's per-scan sums, in shared memory as exact fixed point (kLocal, slot
+// found) or by an L2 vector reduction.  A block met between the first and the
+// last is looked up by its lane alone.  (lookup: insert-or-find, pool index
+// by atomic bump, the block's touch epoch set to this scan's.)
+template <bool kLocal, int kDrop>
+__device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+  const TileSmem t = tile_smem(smem, lb);
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int q = tid; q < kCache; q += kTileThreads) {
+    t.ckey[q] = kEmptyKey;
+    t.cpool[q] = kCachePending;
+  }
+  const TilePoints tp(sc, tile);
+  const int iters = tile_iters(sc);
+  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u;   // this scan's epoch
+  Fixed fx;
+  if (kLocal) {
+    for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
+    uint4* z = reinterpret_cast<uint4*>(t.lo_wd);
+    const int n4 = lb * kVoxPerBlock * 4 / 4;
+    for (int q = tid; q < n4; q += kTileThreads) z[q] = make_uint4(0u, 0u, 0u, 0u);
+    // the fixed-point scale bounds the tile's weights (a cheap pre-pass over
+    // its points; the constant weight is 1)
+    float wm = 1.0f;
+    if (sc.weight_mode != 0) {
+      wm = 0.0f;
+      for (int k = 0; k < iters; ++k) {
+        const long long i = tp.point(sc, k);
+        if (i < 0) continue;
+        float w0;
+        if (sc.weight_mode == 2) {
+          w0 = __ldg(sc.pw + i);
+        } else {
+          const float x = __ldg(sc.pts + 3 * i), y = __ldg(sc.pts + 3 * i + 1), z3 = __ldg(sc.pts + 3 * i + 2);
+          const float zz = sc.sensor == 0 ? z3 * z3 : x * x + y * y + z3 * z3;
+          w0 = 1.0f / zz;
+        }
+        if (isfinite(w0) && w0 >= 0.0f) wm = fmaxf(wm, w0);   // other per-point weights drop their point
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wm = fmaxf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+      if (lane == 0) t.wmax[tid >> 5] = wm;
+    }
+    __syncthreads();
+    if (sc.weight_mode != 0) {
+      wm = 0.0f;
+      for (int w = 0; w < kTileThreads / 32; ++w) wm = fmaxf(wm, t.wmax[w]);
+    }
+    fx = fixed_format(iters * kTileThreads, wm, m.trunc);
+  }
+  __syncthreads();
+
+  const float inv_drop = 1.0f / (m.trunc - m.vs);
+  const float INF = __int_as_float(0x7f800000);
+  unsigned n_obs = 0, n_valid = 0;
+  int* list = t.list + (tid >> 5) * kListPerWarp;
+  for (int k0 = 0; k0 < iters; k0 += kGather) {
+    // gather this warp's candidate points of up to kGather iterations
+    int nl = 0;
+    const int k1 = min(iters, k0 + kGather);
+    for (int k = k0; k < k1; ++k) {
+      const long long i = tp.point(sc, k);
+      const bool ok = i >= 0 && point_candidate(sc, i);
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      if (ok) list[nl + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+      nl += __popc(bal);
+    }
+    __syncwarp();
+    for (int r0 = 0; r0 < nl; r0 += 32) {
+      // ray set-up
+      const int q = r0 + lane;
+      bool act = false;
+      Ray r;
+      float A[3], B[3], w0 = 0.0f;
+      if (q < nl) {
+        const long long i = list[q];
+        if (make_ray(sc, i, r)) {
+          w0 = base_weight(sc, i, r);
+          if (band(r, m.trunc, m.inv_vs, A, B)) act = true;
+          else atomicOr(m.frame_err, kErrKeyRange);
+        }
+      }
+      Walk w;
+      unsigned long long key = 0, key_end = 0;
+      if (act) {
+        int v[3], e[3];
+        walk_init(r, A, B, m.vs, w, v, e);
+        key = pack_key(v[0] >> 3, v[1] >> 3, v[2] >> 3);
+        key_end = pack_key(e[0] >> 3, e[1] >> 3, e[2] >> 3);
+        ++n_valid;
+        n_obs += w.left + 1;
+      }
+      const unsigned actm = __ballot_sync(0xffffffffu, act);
+      if (actm == 0) continue;
+      // the band's first and last blocks, warp-aggregated
+      int slot = -1, pool = -1;
+      warp_lookup<kLocal>(m, t, lb, ep, actm, act, key, slot, pool);
+      int slot_end = slot, pool_end = pool;
+      const bool two = act && key_end != key;
+      const unsigned twom = __ballot_sync(0xffffffffu, two);
+      if (twom) warp_lookup<kLocal>(m, t, lb, ep, twom, two, key_end, slot_end, pool_end);
+      if (!act) continue;
+      // traversal: one observation per cell
+      for (;;) {
+        const float dc = fminf(fmaxf(w.dist, -m.trunc), m.trunc);
+        float wt = w0;
+        if (kDrop != 0 && dc < -m.vs) {
+          const float f = fmaxf((m.trunc + dc) * inv_drop, 0.0f);
+          wt = kDrop == 1 ? wt * f : wt * f * f;
+        }
+        if (kLocal && slot >= 0) {
+          const int e = slot * kVoxPerBlock + w.l;
+          fixed_add(t.lo_wd + e, t.hi_wd + e, fx.S, __float2ll_rn(wt * (dc - m.trunc) * fx.scale));
+          fixed_add(t.lo_w + e, t.hi_w + e, fx.S, __float2ll_rn(wt * fx.scale));
+        } else if (pool >= 0) {
+          red_add2(m.acc + (size_t)pool * kVoxPerBlock + w.l, wt * (dc - m.trunc), wt);
+        }
+        if (w.left == 0) break;
+        --w.left;
+        const bool p1 = w.tm1 < w.tm0;
+        const float t01 = p1 ? w.tm1 : w.tm0;
+        const bool p2 = w.tm2 < t01;
+        const uint32_t inc = p2 ? (1u << 20) : (p1 ? (1u << 10) : 1u);
+        w.nrem -= inc;
+        w.cb -= inc;
+        const float tdb = p2 ? w.td2 : (p1 ? w.td1 : w.td0);
+        const float nt = (w.nrem & (inc << 9)) ? __fadd_rn(p2 ? w.tm2 : t01, tdb) : INF;
+        w.tm0 = (p1 || p2) ? w.tm0 : nt;
+        w.tm1 = (p1 && !p2) ? nt : w.tm1;
+        w.tm2 = p2 ? nt : w.tm2;
+        const int dlb = p2 ? w.dl2 : (p1 ? w.dl1 : w.dl0);
+        w.dist += p2 ? w.dd2 : (p1 ? w.dd1 : w.dd0);
+        w.l += dlb;
+        if ((w.cb & (inc << 3)) == 0) {   // crossed into the neighbouring block
+          w.cb += inc << 3;
+          w.l -= 8 * dlb;
+          const int shift = p2 ? 0 : (p1 ? 21 : 42);
+          key += dlb > 0 ? (1ull << shift) : (0ull - (1ull << shift));
+          if (key == key_end) {
+            slot = slot_end;
+            pool = pool_end;
+          } else {
+            slot = kLocal ? local_slot(t, lb, key) : -1;
+            pool = slot < 0 ? cached_pool(m, t, key, ep) : -1;
+          }
+        }
+      }
+    }
+    __syncwarp();   // the next gather rewrites the list
+  }
+  __syncthreads();
+  if (kLocal) {
+    // allocation: each distinct block of the tile's shared slots is activated once
+    for (int q = tid; q < lb; q += kTileThreads) {
+      const unsigned long long key = t.mkey[q];
+      t.pool[q] = key == kEmptyKey ? -1 : cached_pool(m, t, key, ep);
+    }
+    __syncthreads();
+    // flush the tile's sums into the per-scan accumulators
+    for (int q = 0; q < lb; ++q) {
+      const int pool = t.pool[q];
+      if (pool < 0) continue;
+      float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
+      for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
+        const int e = q * kVoxPerBlock + v;
+        if ((t.lo_w[e] | (unsigned)t.hi_w[e]) == 0u) continue;
+        const float w = fixed_value(t.lo_w[e], t.hi_w[e], fx.S, fx.inv_scale);
+        const float wd = fixed_value(t.lo_wd[e], t.hi_wd[e], fx.S, fx.inv_scale);
+        if (w != 0.0f) red_add2(dst + v, wd, w);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n_obs += __shfl_xor_sync(0xffffffffu, n_obs, o);
+    n_valid += __shfl_xor_sync(0xffffffffu, n_valid, o);
+  }
+  if (lane == 0) {
+    t.red[tid >> 5] = n_obs;
+    t.red[kTileThreads / 32 + (tid >> 5)] = n_valid;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long a = 0, c = 0;
+    for (int w = 0; w < kTileThreads / 32; ++w) {
+      a += t.red[w];
+      c += t.red[kTileThreads / 32 + w];
+    }
+    if (a) atomicAdd(&m.st->obs, a);
+    if (c) atomicAdd(&m.st->valid_pts, c);
+  }
+  __syncthreads();   // shared memory is reused by the caller's next tile
+}
+
 // lb > 0: per-voxel sums of up to lb blocks in shared memory, flushed once per
 // tile; lb == 0: every observation is a vector atomic on the block's global
 // per-scan sums (the L2 performs the float additions).  The accumulation and
@@ -503,28 +801,38 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
 template <bool kCarve>
 __device__ inline void integrate_tile_c(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
   if (lb > 0) {
-    if (sc.dropoff == 0) integrate_tile_t<true, 0, kCarve>(m, sc, tile, smem, lb);
-    else if (sc.dropoff == 1) integrate_tile_t<true, 1, kCarve>(m, sc, tile, smem, lb);
-    else integrate_tile_t<true, 2, kCarve>(m, sc, tile, smem, lb);
+    if (sc.dropoff == 0) integrate_tile_legacy<true, 0, kCarve>(m, sc, tile, smem, lb);
+    else if (sc.dropoff == 1) integrate_tile_legacy<true, 1, kCarve>(m, sc, tile, smem, lb);
+    else integrate_tile_legacy<true, 2, kCarve>(m, sc, tile, smem, lb);
   } else {
-    if (sc.dropoff == 0) integrate_tile_t<false, 0, kCarve>(m, sc, tile, smem, lb);
-    else if (sc.dropoff == 1) integrate_tile_t<false, 1, kCarve>(m, sc, tile, smem, lb);
-    else integrate_tile_t<false, 2, kCarve>(m, sc, tile, smem, lb);
+    if (sc.dropoff == 0) integrate_tile_legacy<false, 0, kCarve>(m, sc, tile, smem, lb);
+    else if (sc.dropoff == 1) integrate_tile_legacy<false, 1, kCarve>(m, sc, tile, smem, lb);
+    else integrate_tile_legacy<false, 2, kCarve>(m, sc, tile, smem, lb);
   }
 }
 
-// Any scan: accumulation mode, drop-off and carving chosen at run time
-// (carved rays keep the ray for exact distances near the band, which costs
+template <bool kLocal>
+__device__ inline void integrate_tile_d(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
+  if (sc.dropoff == 0) integrate_tile_t<kLocal, 0>(m, sc, tile, smem, lb);
+  else if (sc.dropoff == 1) integrate_tile_t<kLocal, 1>(m, sc, tile, smem, lb);
+  else integrate_tile_t<kLocal, 2>(m, sc, tile, smem, lb);
+}
+
+// Any scan: accumulation mode, drop-off and form chosen at run time (carved
+// rays and very long bands take the general per-thread form, whose extra
 // registers the plain variants need not hold).
 __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
   if (sc.carve) integrate_tile_c<true>(m, sc, tile, smem, lb);
-  else integrate_tile_c<false>(m, sc, tile, smem, lb);
+  else if (sc.long_band) integrate_tile_c<false>(m, sc, tile, smem, lb);
+  else if (lb > 0) integrate_tile_d<true>(m, sc, tile, smem, lb);
+  else integrate_tile_d<false>(m, sc, tile, smem, lb);
 }
 
 // Variant index of a scan: accumulation mode x drop-off (0..5), so a launch
 // whose scans share one variant runs a kernel holding only that code.
-__host__ __device__ inline int tile_variant(int lb, int dropoff, int carve) {
-  return carve ? -1 : (lb > 0 ? 3 : 0) + dropoff;   // -1: the run-time dispatching kernel
+// general: carving or bands longer than 512 cells per axis.
+__host__ __device__ inline int tile_variant(int lb, int dropoff, int general) {
+  return general ? -1 : (lb > 0 ? 3 : 0) + dropoff;   // -1: the run-time dispatching kernel
 }
 
 template <int kVariant>
@@ -543,8 +851,8 @@ struct Vox4;
 template <>
 struct Vox4<0> {
   static __device__ __forceinline__ void load(const SubmapDev& m, size_t e, float D[4], float W[4]) {
-    const float4 d = *reinterpret_cast<const float4*>((const float*)m.D + e);
-    const float4 w = *reinterpret_cast<const float4*>((const float*)m.W + e);
+    const float4 d = __ldcg(reinterpret_cast<const float4*>((const float*)m.D + e));
+    const float4 w = __ldcg(reinterpret_cast<const float4*>((const float*)m.W + e));
     D[0] = d.x; D[1] = d.y; D[2] = d.z; D[3] = d.w;
     W[0] = w.x; W[1] = w.y; W[2] = w.z; W[3] = w.w;
   }
@@ -557,8 +865,8 @@ struct Vox4<0> {
 template <>
 struct Vox4<1> {   // FP16 storage: D / trunc and W as IEEE half, FP32 arithmetic
   static __device__ __forceinline__ void load(const SubmapDev& m, size_t e, float D[4], float W[4]) {
-    const uint2 d = *reinterpret_cast<const uint2*>((const __half*)m.D + e);
-    const uint2 w = *reinterpret_cast<const uint2*>((const __half*)m.W + e);
+    const uint2 d = __ldcg(reinterpret_cast<const uint2*>((const __half*)m.D + e));
+    const uint2 w = __ldcg(reinterpret_cast<const uint2*>((const __half*)m.W + e));
     const __half2* dh = reinterpret_cast<const __half2*>(&d);
     const __half2* wh = reinterpret_cast<const __half2*>(&w);
     const float2 d0 = __half22float2(dh[0]), d1 = __half22float2(dh[1]);
@@ -579,28 +887,21 @@ struct Vox4<1> {   // FP16 storage: D / trunc and W as IEEE half, FP32 arithmeti
   }
 };
 
-// Merge the sums of touched blocks j0 and j1 (j1 < 0: none) with
+// Merge the sums of blocks p0 and p1 (pool indices; p1 < 0: none) with
 // kMergeThreads threads, this one being `tid` (4 voxels of each block).  All
 // loads of both blocks are issued before any result is used, so two blocks'
-// dependent chains overlap.  Returns the voxels merged by this thread.
-template <int kStore>
-__device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, bool skip, int tid);
-
-template <int kStore>
-__device__ __forceinline__ int merge_two(const SubmapDev& m, int j0, int j1, bool skip, int tid) {
-  return merge_pools<kStore>(m, m.touched[j0], j1 >= 0 ? m.touched[j1] : -1, skip, tid);
-}
-
-// The same for blocks given by pool index (p1 < 0: none).
+// dependent chains overlap.  Sums, D and W are read from the L2 (.cg): in the
+// persistent kernels they were last written by other SMs.  Returns the
+// voxels merged by this thread.
 template <int kStore>
 __device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, bool skip, int tid) {
   float4* a = reinterpret_cast<float4*>(m.acc + (size_t)p0 * kVoxPerBlock) + 2 * tid;
   float4* b = p1 >= 0 ? reinterpret_cast<float4*>(m.acc + (size_t)p1 * kVoxPerBlock) + 2 * tid : nullptr;
-  const float4 a0 = a[0], a1 = a[1];
+  const float4 a0 = __ldcg(a), a1 = __ldcg(a + 1);
   float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
   if (b) {
-    b0 = b[0];
-    b1 = b[1];
+    b0 = __ldcg(b);
+    b1 = __ldcg(b + 1);
   }
   const float swa[4] = {a0.x, a0.z, a1.x, a1.z}, wa[4] = {a0.y, a0.w, a1.y, a1.w};
   const float swb[4] = {b0.x, b0.z, b1.x, b1.z}, wb[4] = {b0.y, b0.w, b1.y, b1.w};
@@ -641,16 +942,41 @@ __device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, b
     b[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     b[1] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (tid == 0 && m.touch) {
-    m.touch[p0] = -1;
-    if (p1 >= 0) m.touch[p1] = -1;
-  }
   return merged;
 }
 
-template <int kStore>
-__device__ __forceinline__ int merge_block(const SubmapDev& m, int j, bool skip, int tid) {
-  return merge_two<kStore>(m, j, -1, skip, tid);
+// Merge of a span of kSpanBlocks consecutive pool indices [p0, p0 + n) by a
+// 256-thread CTA: the span's touch epochs are read in one round (.cg), the
+// blocks holding the scan's epoch `ep` compacted into shared memory with a
+// warp ballot, then merged two per half CTA.  Returns this thread's merged
+// voxels; *touched (every thread) gets the span's touched blocks.
+constexpr int kSpanBlocks = 32;
+
+struct SpanList {
+  int pool[kSpanBlocks];
+  int n;
+};
+
+__device__ __forceinline__ int merge_span(const SubmapDev& m, int p0, int n, uint32_t ep, bool skip, SpanList* sl,
+                                          int* touched) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const bool t = tid < n && __ldcg(m.tepoch + p0 + tid) == ep;
+    const unsigned bal = __ballot_sync(0xffffffffu, t);
+    if (t) sl->pool[__popc(bal & ((1u << tid) - 1u))] = p0 + tid;
+    if (tid == 0) sl->n = __popc(bal);
+  }
+  __syncthreads();
+  const int cnt = sl->n;
+  const int half = tid / kMergeThreads, sub = tid % kMergeThreads;
+  int merged = 0;
+  for (int k = 2 * half; k < cnt; k += 4) {
+    const int q = k + 1 < cnt ? sl->pool[k + 1] : -1;
+    merged += m.storage == 0 ? merge_pools<0>(m, sl->pool[k], q, skip, sub) : merge_pools<1>(m, sl->pool[k], q, skip, sub);
+  }
+  *touched = cnt;
+  __syncthreads();   // the list is rewritten by the next span
+  return merged;
 }
 
 }  // namespace covox

@@ -505,6 +505,54 @@ __global__ void __launch_bounds__(32 * kIWarps) mlp_infer_kernel(const float* __
   }
 }
 
+// Target normalisation: per-CTA partial sums of e2 * mask and mask over a
+// fixed grid-stride partition, summed in CTA order by one thread (so the mean
+// does not depend on scheduling), then every target divided by the mean.
+constexpr int kNormCtas = 256;
+
+__global__ void __launch_bounds__(256) target_sums_kernel(const float* __restrict__ e2,
+                                                          const float* __restrict__ mask, long long n,
+                                                          double* __restrict__ partial) {
+  __shared__ double se[256], sm[256];
+  double a = 0.0, c = 0.0;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    a += (double)e2[i] * (double)mask[i];
+    c += (double)mask[i];
+  }
+  se[threadIdx.x] = a;
+  sm[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      se[threadIdx.x] += se[threadIdx.x + o];
+      sm[threadIdx.x] += sm[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = se[0];
+    partial[2 * blockIdx.x + 1] = sm[0];
+  }
+}
+
+__global__ void target_scale_kernel(float* __restrict__ e2, long long n, const double* __restrict__ partial,
+                                    int nparts, float* __restrict__ mean_out) {
+  __shared__ float inv;
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+      a += partial[2 * p];
+      c += partial[2 * p + 1];
+    }
+    const float mean = (float)(a / (c > 1.0 ? c : 1.0));
+    if (blockIdx.x == 0) *mean_out = mean;
+    inv = mean > 0.0f ? 1.0f / mean : 1.0f;
+  }
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    e2[i] *= inv;
+}
+
 // Fixed-order sum of the CTA partials, mean over valid points, Adam.
 __global__ void adam_kernel(float* __restrict__ params, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ partial, int nparts, float lr, float b1, float b2,
@@ -645,6 +693,31 @@ cvx_status cvx_weight_model_last(cvx_weight_model* w, float* grad, float* loss, 
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
+  return CVX_OK;
+}
+
+cvx_status cvx_normalise_targets(float* e2, const float* mask, int64_t n, float* mean_out, void* stream) {
+  if (!e2 || !mask || !mean_out || n <= 0) return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* partial = nullptr;
+  float* mean_dev = nullptr;
+  // a small scratch of partials: stream-ordered allocation, freed on the stream
+  if (cudaMallocAsync((void**)&partial, sizeof(double) * 2 * kNormCtas + 16, s) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_OOM;
+  }
+  mean_dev = (float*)(partial + 2 * kNormCtas);
+  COVOX_LAUNCH(kKTargets, s, target_sums_kernel<<<kNormCtas, 256, 0, s>>>(e2, mask, n, partial));
+  const int grid = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
+  COVOX_LAUNCH(kKTargets, s, target_scale_kernel<<<grid, 256, 0, s>>>(e2, n, partial, kNormCtas, mean_dev));
+  float mean = 0.0f;
+  const bool ok = cudaMemcpyAsync(&mean, mean_dev, sizeof(float), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                  cudaFreeAsync(partial, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  *mean_out = mean;
   return CVX_OK;
 }
 

@@ -6,7 +6,7 @@
 // process's allocator.  For them,
 // cvx_integrate_scan_noalloc() integrates a scan into submap storage the
 // caller already owns (a cvx_submap_view) and keeps its per-scan scratch (the
-// per-voxel sums and the touched-block list) in one file-scope device array
+// per-voxel sums and the blocks' touch epochs) in one file-scope device array
 // of fixed size.  It runs the same device functions as cvx_integrate_scan.
 //
 // The scratch array is a host-side symbol in host code: its device address is
@@ -30,10 +30,10 @@ using namespace covox;
 namespace {
 
 constexpr size_t kAccBytes = (size_t)CVX_NOALLOC_MAX_BLOCKS * kVoxPerBlock * sizeof(float2);
-constexpr size_t kListBytes = (size_t)CVX_NOALLOC_MAX_BLOCKS * sizeof(int32_t);
-constexpr size_t kScratchBytes = kAccBytes + 2 * kListBytes;
+constexpr size_t kEpochBytes = (size_t)CVX_NOALLOC_MAX_BLOCKS * sizeof(uint32_t);
+constexpr size_t kScratchBytes = kAccBytes + kEpochBytes;
 
-// per-scan sums | touch map | touched list
+// per-scan sums | touch epochs of the blocks
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 static_assert(sizeof(State) <= CVX_SUBMAP_STATE_BYTES, "state buffer too small");
@@ -76,29 +76,34 @@ __global__ void __launch_bounds__(kTileThreads) integrate_static_kernel(SubmapDe
   integrate_tile(m, sc, blockIdx.x, smem, lb);
 }
 
-__global__ void __launch_bounds__(kMergeThreads) merge_static_kernel(SubmapDev m) {
-  __shared__ unsigned long long red[kMergeThreads / 32];
-  const int nt = min(*((volatile int32_t*)m.n_touched), m.max_blocks);
+// The scan's epoch is 1: the touch epochs are cleared before every call.
+__global__ void __launch_bounds__(kTileThreads) merge_static_kernel(SubmapDev m) {
+  __shared__ unsigned long long red[kTileThreads / 32];
+  __shared__ SpanList sl;
+  const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
   const bool skip = *((volatile int32_t*)m.frame_err) != 0;
-  unsigned long long merged = 0;
-  for (int j = blockIdx.x; j < nt; j += gridDim.x) merged += merge_block<0>(m, j, skip, threadIdx.x);
+  unsigned long long merged = 0, touched = 0;
+  for (int p0 = blockIdx.x * kSpanBlocks; p0 < nb; p0 += gridDim.x * kSpanBlocks) {
+    int t = 0;
+    merged += merge_span(m, p0, min(kSpanBlocks, nb - p0), 1u, skip, &sl, &t);
+    touched += t;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) merged += __shfl_xor_sync(0xffffffffu, merged, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = merged;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int w = 0; w < kMergeThreads / 32; ++w) t += red[w];
+    for (int w = 0; w < kTileThreads / 32; ++w) t += red[w];
     if (t) atomicAdd(&m.st->voxels_merged, t);
+    if (touched) atomicAdd(&m.st->blocks_touched, touched);
     __threadfence();
     if (atomicAdd(&m.st->ticket, 1u) == gridDim.x - 1) {
       __threadfence();
       State* st = m.st;
-      st->blocks_touched += (unsigned long long)nt;
       st->frames += 1;
       st->sticky_err |= *m.frame_err;
       *m.frame_err = 0;
-      *m.n_touched = 0;
       st->ticket = 0;
     }
   }
@@ -150,16 +155,13 @@ extern "C" cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, co
   m.D = view->dist;
   m.W = view->weight;
   m.st = (State*)view->state;
-  m.n_touched = &m.st->n_touched;
   m.frame_err = &m.st->frame_err;
   unsigned char* base = (unsigned char*)scratch;
   m.acc = (float2*)base;
-  m.touch = (int32_t*)(base + kAccBytes);
-  m.touched = (int32_t*)(base + kAccBytes + kListBytes);
+  m.tepoch = (uint32_t*)(base + kAccBytes);
   m.slot_mask = (uint32_t)(view->hash_slots - 1);
   m.max_probe = (int)(view->hash_slots < 4096 ? view->hash_slots : 4096);
   m.max_blocks = (int)view->max_blocks;
-  m.max_touched = (int)view->max_blocks;
   m.vs = view->voxel_size;
   m.inv_vs = 1.0f / view->voxel_size;
   m.trunc = view->trunc;
@@ -168,20 +170,22 @@ extern "C" cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, co
 
   cudaStream_t s = (cudaStream_t)stream;
   // The scratch keeps the previous call's contents: clear the sums, the
-  // touch map and this scan's fields of the caller's state.
+  // touch epochs and this scan's fields of the caller's state (error bits,
+  // merge ticket, epoch: the scan's epoch is 1).
   const size_t acc_bytes = (size_t)view->max_blocks * kVoxPerBlock * sizeof(float2);
   if (cudaMemsetAsync(m.acc, 0, acc_bytes, s) != cudaSuccess ||
-      cudaMemsetAsync(m.touch, 0xff, (size_t)view->max_blocks * sizeof(int32_t), s) != cudaSuccess ||
-      cudaMemsetAsync((char*)view->state + offsetof(State, n_touched), 0, 2 * sizeof(int32_t), s) !=
-          cudaSuccess ||
-      cudaMemsetAsync((char*)view->state + offsetof(State, ticket), 0, sizeof(uint32_t), s) != cudaSuccess) {
+      cudaMemsetAsync(m.tepoch, 0, (size_t)view->max_blocks * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync((char*)view->state + offsetof(State, frame_err), 0, sizeof(int32_t), s) != cudaSuccess ||
+      cudaMemsetAsync((char*)view->state + offsetof(State, ticket), 0, sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync((char*)view->state + offsetof(State, epoch), 0, sizeof(uint32_t), s) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
   if (n == 0) return CVX_OK;
   COVOX_LAUNCH(kKAccum, s,
                integrate_static_kernel<<<sc.n_tiles, kTileThreads, tile_smem_bytes(lb), s>>>(m, sc, lb));
-  const int grid = m.max_blocks < num_sms() * 2 ? m.max_blocks : num_sms() * 2;
-  COVOX_LAUNCH(kKMerge, s, merge_static_kernel<<<grid, kMergeThreads, 0, s>>>(m));
+  const int spans = (m.max_blocks + kSpanBlocks - 1) / kSpanBlocks;
+  const int grid = spans < num_sms() * 2 ? spans : num_sms() * 2;
+  COVOX_LAUNCH(kKMerge, s, merge_static_kernel<<<grid, kTileThreads, 0, s>>>(m));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }

@@ -23,7 +23,8 @@ enum KernelKind : int {
   kKPipeClose = 12, // pipelined per-scan bookkeeping after each scan
   kKEsdf = 13,      // distance field of a submap
   kKHash = 14,      // stand-alone block hash insert / find
-  kNumKinds = 15
+  kKDiscard = 15,   // reset: per-scan sums a launch left unmerged
+  kNumKinds = 16
 };
 
 void prof_begin(int kind, cudaStream_t s);

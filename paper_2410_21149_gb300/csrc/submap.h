@@ -78,6 +78,7 @@ inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t
   sc->dropoff = ip->dropoff;
   sc->sensor = ip->sensor;
   sc->carve = (ip->flags & CVX_INTEGRATE_CARVE) ? 1 : 0;
+  sc->long_band = (double)map->p.trunc / (double)map->p.voxel_size < 250.0 ? 0 : 1;
   sc->organised = (ip->height > 0 && ip->width >= 32 && (int64_t)ip->height * ip->width == n) ? 1 : 0;
   sc->height = ip->height;
   sc->width = ip->width;

@@ -110,12 +110,12 @@ def build_training_set(noisy_scans: Sequence, clean_scans: Sequence, voxel_size:
 
 
 def normalise_targets(e2, mask):
-    """Targets divided by their mean over valid points: the fitted weights are
-    then ~1 for a typical point (the scale of the constant weight), so the
-    stored weight's cap is met no sooner than with the plain weighting.
-    Returns (e2 / mean, mean)."""
-    mean = float((e2 * mask).sum() / mask.sum().clamp(min=1))
-    return e2 / mean, mean
+    """Targets divided by their mean over valid points (cvx_normalise_targets,
+    in place on the device): the fitted weights are then ~1 for a typical
+    point, the scale of the constant weight.  Returns (e2, mean)."""
+    e2 = e2.contiguous()
+    mean = _capi.cvx_normalise_targets(e2, mask.contiguous())
+    return e2, mean
 
 
 def train(model: WeightModel, feats, e2, mask, steps: int = 400, batch: int = 65536, lr: float = 3e-3,

@@ -205,3 +205,20 @@ def test_learned_weight_gain_over_plain_weighting():
     keep = weights.gate(res["learned"]["sdf_rmse"], res["quadratic"]["sdf_rmse"])
     assert keep == (res["learned"]["sdf_rmse"] < res["quadratic"]["sdf_rmse"])
     model.close()
+
+
+def test_normalise_targets_on_device():
+    """cvx_normalise_targets: e2 divided in place by its mean over the mask
+    (the scale the learned weights are fitted at), deterministic."""
+    import torch
+    from paper_2410_21149_gb300 import weights
+    rng = np.random.default_rng(9)
+    n = 1_000_003
+    e2 = rng.uniform(1e-5, 1e-2, n).astype(np.float32)
+    mask = (rng.uniform(size=n) > 0.3).astype(np.float32)
+    mean_ref = float((e2.astype(np.float64) * mask).sum() / mask.sum())
+    out, mean = weights.normalise_targets(torch.from_numpy(e2).cuda(), torch.from_numpy(mask).cuda())
+    assert abs(mean / mean_ref - 1) < 1e-6
+    assert np.allclose(out.cpu().numpy(), e2 / np.float32(mean), rtol=2e-7, atol=0)
+    out2, mean2 = weights.normalise_targets(torch.from_numpy(e2).cuda(), torch.from_numpy(mask).cuda())
+    assert mean2 == mean and torch.equal(out, out2)

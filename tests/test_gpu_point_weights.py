@@ -67,9 +67,10 @@ def test_trained_network_weights_multiroom(trained_weights, lb, ppc):
     assert np.isfinite(w).all() and w.min() > 0 and w.max() / w.min() > 3   # not a constant
     g = run_gpu(wl, point_weights=pw, weight_mode=2, local_blocks=lb, pts_per_cta=ppc)[0]
     o = run_oracle(wl, point_weights=pw, weight_mode=2)[0]
-    r = compare(g, o, D_TOL)
+    fl = _dropoff_floor(wl, float(w.max()))
+    r = compare(g, o, D_TOL, w_floor=fl, d_tol_w=2 * wl.submaps[0].trunc * (fl if wl.dropoff else 0.0))
     _counts_match(g, o)
-    assert r["voxels"] > 100000
+    assert r["voxels"] > 50000
 
 
 @pytest.mark.parametrize("lb", [-1, 2])
@@ -87,8 +88,27 @@ def test_weights_spanning_five_decades(lb, dropoff):
         pw.append(w)
     g = run_gpu(wl, point_weights=[pw], weight_mode=2, local_blocks=lb, pts_per_cta=512)[0]
     o = run_oracle(wl, point_weights=[pw], weight_mode=2)[0]
-    compare(g, o, D_TOL)
+    fl = _dropoff_floor(wl, float(np.concatenate(pw).max()))
+    compare(g, o, D_TOL, w_floor=fl, d_tol_w=2 * wl.submaps[0].trunc * (fl if dropoff else 0.0))
     _counts_match(g, o)
+
+
+def _dropoff_floor(wl, w0_max, d_err=1e-6):
+    """W tolerance floor of a drop-off run: behind the surface the weight is
+    w0 (trunc + d) / (trunc - vs), so the FP32 distance of a cell moves an
+    observation's weight by w0 dd / (trunc - vs).  A cell's FP32 distance is
+    within 1e-7 m of the FP64 one after a band's incremental steps (an FP32
+    emulation of 16 steps on 2e5 random rays peaks at 9.5e-8 m), and a voxel
+    gathers at most ~10 tail observations per frame here: d_err = 1e-6 m.  A
+    voxel whose W is small next to the base weights of the points that reach
+    it deep in the tail can therefore not meet a purely relative bound; the
+    constant 1e-6 floor of the other tests is this term for w0 <= 0.1.  The
+    same weight errors move a voxel's weighted mean distance by at most
+    2 trunc floor / W (its distances lie within [-trunc, trunc])."""
+    sm = wl.submaps[0]
+    if wl.dropoff == 0:
+        return 1e-6
+    return max(1e-6, w0_max * d_err / (sm.trunc - sm.voxel_size))
 
 
 @pytest.mark.parametrize("lb", [-1, 4])

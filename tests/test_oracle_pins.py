@@ -471,3 +471,20 @@ def test_carving_extends_the_band():
         assert all(carved[k] == band[k] for k in band)
         extra = [carved[k] for k in carved if k not in band]
         assert extra and all(abs(d - 0.3) < 1e-6 and w == 1.0 for d, w in extra)
+
+
+def test_parallel_frame_sums_equal_sequential():
+    """The OpenMP form of a frame (chunked per-thread sums added in chunk
+    order) gives the sequential frame's blocks, counts and values up to FP64
+    rounding of the sums' order (commutative sums, Sec. III-D)."""
+    scene, scans, poses = _small_scan()
+    a = orc.OracleSubmap(0.1, 0.3, 1e4)
+    b = orc.OracleSubmap(0.1, 0.3, 1e4)
+    for s, T in zip(scans, poses):
+        sa = a.integrate(s, T, None, 1, 1)
+        sb = b.integrate_parallel(s, T, 4, None, 1, 1)
+        assert sa == sb
+    ka, Da, Wa = a.extract()
+    kb, Db, Wb = b.extract()
+    assert np.array_equal(ka, kb)
+    assert np.allclose(Da, Db, rtol=0, atol=1e-12) and np.allclose(Wa, Wb, rtol=1e-12, atol=0)
