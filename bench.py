@@ -326,9 +326,9 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
             "reset_and_other_ms": ms_b - kern_ms, "pipelined": pipelined,
             "e2e_ms_per_step": e2e_ms, "h2d_bytes_per_step": int(n_points * 12),
             "d2h_bytes_per_step": 48 * len(subs),
-            "phases": {"waves": int(len(phases)), "tiles_ms": float(phases[:, 0].sum()),
-                       "merge_ms": float(phases[:, 1].sum()), "bookkeeping_ms": float(phases[:, 2].sum()),
-                       "per_wave_median_ms": [float(x) for x in np.median(phases, 0)]}}
+            "phases": {"scans": int(len(phases)), "last_tiles_done_ms": float(phases[:, 0].max()),
+                       "last_merged_ms": float(phases[:, 1].max()),
+                       "median_tiles_done_to_merged_ms": float(np.median(phases[:, 1] - phases[:, 0]))}}
 
 
 # -------------------------------------------------------------- our arm
@@ -724,7 +724,6 @@ def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     N = sm.scans[0].points.shape[0]
-    feats = torch.empty((N, 3), dtype=torch.float32, device="cuda")
     wbuf = torch.empty(N, dtype=torch.float32, device="cuda")
     prm = cvx.integrate_params(cvx.CVX_W_PER_POINT, wl.dropoff, wl.min_range, wl.max_range, 0, H, W, args.ppc,
                                args.lb)
@@ -734,8 +733,8 @@ def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):
     def step():
         sub.reset(stream)
         for f in range(len(Ts)):
-            _capi.cvx_point_features(pts[f], H, W, 0, wl.max_range, feats, stream)
-            _capi.cvx_weight_model_infer(model.handle, feats, wbuf, stream)
+            # features + network in one fused kernel, then the per-point-weight integration
+            _capi.cvx_weight_model_point_weights(model.handle, pts[f], H, W, 0, wl.max_range, wbuf, stream)
             sub.integrate(pts[f], Ts[f], prm, wbuf, stream)
 
     for _ in range(2):

@@ -211,6 +211,18 @@ cvx_status cvx_registration_points(cvx_submap* map, float w_min, float d_band, i
  * Synchronises `stream`. */
 cvx_status cvx_submap_bounds(cvx_submap* map, float lo_hi[6], void* stream);
 
+/* Overlap of posed submaps (Sec. III-F: the backend registers submaps whose
+ * boxes overlap).  bounds: device float32 [n,6], each submap's lo_hi from
+ * cvx_submap_bounds (submap frame; lo > hi marks an empty submap); poses:
+ * device float32 [n,12], 3x4 row-major world <- submap.  For every ordered
+ * pair (i, j): each box carried to the world frame (the axis-aligned box of
+ * its 8 transformed corners), the two intersected; volume[i*n + j] (device
+ * float32 [n,n], m^3) is the intersection's volume, 0 if disjoint or empty;
+ * boxes (device float32 [n,n,6] or NULL) receives the intersection lo, hi.
+ * Asynchronous on `stream`. */
+cvx_status cvx_submap_overlaps(int32_t n, const float* bounds, const float* poses, float* volume, float* boxes,
+                               void* stream);
+
 /* Free the submap and everything it allocated (synchronises its stream). */
 void cvx_destroy(cvx_submap* map);
 
@@ -270,47 +282,51 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
  * persistent kernel (Sec. III-D workload equalisation across scans).  Scans
  * of one submap are integrated as successive frames in array order (exactly
  * as successive cvx_integrate_scan calls); scans of different submaps are
- * independent; empty scans are skipped.  The scans' tiles of each wave (the
- * k-th scan of every submap) are spread over all SMs, then all touched blocks
- * are merged.  Asynchronous on `stream`; the descriptor upload reads the
- * batch object's pinned staging buffer when the stream executes it, so a CUDA
- * graph that captured this call replays the staging buffer's contents at
- * replay time: do not issue another call on the same batch object between
- * replays.  Grid barriers inside the kernel are bounded; a barrier that gives
- * up is reported by cvx_batch_error() as CVX_ERR_TIMEOUT, after which the
- * batch's submaps must be reset. */
+ * independent; empty scans are skipped.  The kernel takes tile and merge
+ * work items from one queue in dependency order (a scan's tiles wait for the
+ * merge that last used their per-scan set -- with pipelined submaps, two
+ * sets, so consecutive scans overlap --, a scan's merge for its tiles and for
+ * the previous scan's merge), so no grid-wide barrier is needed.  Asynchronous
+ * on `stream`; the descriptor upload reads the batch object's pinned staging
+ * buffer when the stream executes it, so a CUDA graph that captured this call
+ * replays the staging buffer's contents at replay time: do not issue another
+ * call on the same batch object between replays.  Every wait inside the
+ * kernel is bounded; a wait that gives up is reported by cvx_batch_error() as
+ * CVX_ERR_TIMEOUT, after which the batch's submaps must be reset. */
 cvx_status cvx_integrate_batch(cvx_batch* batch, cvx_submap* const* maps, int32_t n_maps,
                                const cvx_scan_desc* scans, int32_t n_scans, void* stream);
 
-/* Tuning: cut every wave into chunks of at most max_scans_per_wave scans (0 =
- * no limit).  Smaller waves keep each wave's per-scan sums resident in L2 at
- * the cost of more grid barriers.  Results do not depend on it. */
+/* Tuning: the queue takes the scans in rounds (round k: the k-th scan of
+ * every submap, its merges in the next round); this cuts every round into
+ * chunks of at most max_scans_per_wave scans (0 = no limit), which bounds the
+ * submaps in flight.  Results do not depend on it. */
 cvx_status cvx_batch_wave_limit(cvx_batch* batch, int32_t max_scans_per_wave);
 
-/* CVX_ERR_TIMEOUT if a barrier of the last batch gave up (synchronous). */
+/* CVX_ERR_TIMEOUT if a wait of the last batch gave up (synchronous). */
 int32_t cvx_batch_error(cvx_batch* batch);
 
-/* Test hook for the bounded grid barriers (off by default): while
- * missing_cta >= 0, that CTA of this batch's launches leaves before its first
- * barrier arrival, and the barriers give up after barrier_polls polls
- * (<= 0: the default limit, about one second).  The other CTAs then wait out
- * the limit and return; cvx_batch_error() reports CVX_ERR_TIMEOUT and the
- * submaps must be reset.  missing_cta < 0 restores normal launches.  Nothing
- * faults or hangs: it exercises the timeout path the barriers always have. */
+/* Test hook for the bounded waits (off by default): while missing_cta >= 0,
+ * that CTA of this batch's launches takes one work item and leaves without
+ * doing it, and the waits give up after barrier_polls polls (<= 0: the
+ * default limit, about one second).  The CTAs waiting for the item run out
+ * their limit and the launch drains; cvx_batch_error() reports
+ * CVX_ERR_TIMEOUT (also when nothing waited for the item: the last CTA to
+ * leave checks that every scan was merged) and the submaps must be reset.
+ * missing_cta < 0 restores normal launches.  Nothing faults or hangs: it
+ * exercises the timeout path the waits always have. */
 cvx_status cvx_batch_test_missing_cta(cvx_batch* batch, int32_t missing_cta, int64_t barrier_polls);
 
 void cvx_batch_destroy(cvx_batch* batch);
 
-/* Tracing of the batched kernel: with timing enabled, CTA 0 stamps the GPU
- * global timer after each grid barrier; cvx_batch_phase_times() (synchronous)
- * returns, for each wave of the last batch, the milliseconds of phase 1
- * (tiles), phase 2 (merges) and phase 3 (bookkeeping), each including its
- * barrier: ms[3 * wave + phase].  When every submap of the batch is
- * pipelined, the entries are per step instead (n_waves + 1 steps): phase 1 =
- * tiles of wave w together with the merges of wave w - 1, phase 2 = the
- * bookkeeping of wave w - 1, phase 3 = 0.  Returns the entries written. */
+/* Tracing of the batched kernel: with timing enabled, the kernel stamps the
+ * GPU global timer at its start, when the last tile of each scan finishes and
+ * when each scan's merge completes; cvx_batch_phase_times() (synchronous)
+ * returns, for each scan of the last batch in queue order (rounds of equal
+ * rank), the milliseconds from the launch start to its tiles' end
+ * (ms[3 * scan]) and to its merge's end (ms[3 * scan + 1]; ms[3 * scan + 2] =
+ * 0).  Returns the scans written (at most max_scans). */
 cvx_status cvx_batch_timing(cvx_batch* batch, int32_t enable);
-int32_t cvx_batch_phase_times(cvx_batch* batch, double* ms, int32_t max_waves);
+int32_t cvx_batch_phase_times(cvx_batch* batch, double* ms, int32_t max_scans);
 
 /* ---- learned per-point weight (Sec. III-C weighting paragraph) ----
  * Features of an organised scan, one row of three per point (device float32
@@ -337,6 +353,13 @@ cvx_status cvx_weight_model_params(cvx_weight_model* model, const float* set, fl
 /* weights[i] = network(features[i]) for n points (device arrays). */
 cvx_status cvx_weight_model_infer(cvx_weight_model* model, const float* features, int64_t n,
                                   float* weights, void* stream);
+/* Per-point weights of an organised scan in one pass: the features of
+ * cvx_point_features and the network of cvx_weight_model_infer, computed
+ * together (the features never leave the chip).  points_xyz: device float32
+ * [height*width, 3]; weights: device float32 [height*width]. */
+cvx_status cvx_weight_model_point_weights(cvx_weight_model* model, const float* points_xyz, int32_t height,
+                                          int32_t width, int32_t sensor, float max_range, float* weights,
+                                          void* stream);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr; lr = 0 only
  * computes the gradient) on the mean over points with mask != 0 of
  * w e2 - ln w (Gaussian negative log likelihood of precision w).  The

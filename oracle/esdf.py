@@ -131,3 +131,27 @@ def submap_bounds(keys, vs) -> np.ndarray:
     keys = np.asarray(keys).astype(np.float32)
     bs = np.float32(8) * np.float32(vs)
     return np.concatenate([keys.min(0) * bs, (keys.max(0) + 1) * bs]).astype(np.float32)
+
+
+def submap_overlap(bounds_i, T_i, bounds_j, T_j):
+    """Intersection of two posed submaps' boxes (Sec. III-F, the backend's AABB
+    overlap test), FP64: each block-corner box (submap frame) carried to the
+    world frame by its pose (3x4 world <- submap) as the axis-aligned box of
+    its 8 transformed corners, the two boxes intersected.  Returns (volume,
+    lo_hi [6]); volume 0 when disjoint or when a box is empty (lo > hi)."""
+    def world(b, T):
+        b = np.asarray(b, np.float64)
+        T = np.asarray(T, np.float64).reshape(3, 4)
+        corners = np.array([[b[3] if c & 1 else b[0], b[4] if c & 2 else b[1], b[5] if c & 4 else b[2]]
+                            for c in range(8)])
+        w = corners @ T[:, :3].T + T[:, 3]
+        return w.min(0), w.max(0)
+
+    bi, bj = np.asarray(bounds_i, np.float64), np.asarray(bounds_j, np.float64)
+    li, hi_ = world(bi, T_i)
+    lj, hj = world(bj, T_j)
+    lo, hi = np.maximum(li, lj), np.minimum(hi_, hj)
+    empty = (bi[:3] > bi[3:]).any() or (bj[:3] > bj[3:]).any()
+    vol = 0.0 if empty else float(np.prod(np.maximum(hi - lo, 0.0)))
+    return vol, np.concatenate([lo, hi])
+

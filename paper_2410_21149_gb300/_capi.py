@@ -94,6 +94,7 @@ SIGNATURES = {
     "cvx_flush_submap": (_i32, [_vp, _vp]),
     "cvx_registration_points": (_i32, [_vp, ctypes.c_float, ctypes.c_float, _i64, _vp, _vp, _vp]),
     "cvx_submap_bounds": (_i32, [_vp, _vp, _vp]),
+    "cvx_submap_overlaps": (_i32, [_i32, _vp, _vp, _vp, _vp, _vp]),
     "cvx_block_hash_create": (_i32, [_i64, _i64, _vp]),
     "cvx_block_hash_insert": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "cvx_block_hash_find": (_i32, [_vp, _vp, _i64, _vp, _vp]),
@@ -116,6 +117,7 @@ SIGNATURES = {
     "cvx_weight_model_create": (_i32, [_vp, ctypes.POINTER(_vp)]),
     "cvx_weight_model_params": (_i32, [_vp, _vp, _vp, _vp]),
     "cvx_weight_model_infer": (_i32, [_vp, _vp, _i64, _vp, _vp]),
+    "cvx_weight_model_point_weights": (_i32, [_vp, _vp, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "cvx_weight_model_train_step": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, _vp]),
     "cvx_weight_model_last": (_i32, [_vp, _vp, _vp, _vp]),
     "cvx_weight_model_destroy": (None, [_vp]),
@@ -227,10 +229,11 @@ def cvx_batch_timing(batch: int, enable: bool) -> None:
     check(lib().cvx_batch_timing(batch, int(enable)), "cvx_batch_timing")
 
 
-def cvx_batch_phase_times(batch: int, max_waves: int = 1 << 16) -> np.ndarray:
-    """[waves, 3] milliseconds of phase 1 (tiles), 2 (merge), 3 (bookkeeping)."""
-    out = np.zeros(3 * max_waves, np.float64)
-    n = lib().cvx_batch_phase_times(batch, out.ctypes.data_as(ctypes.c_void_p), max_waves)
+def cvx_batch_phase_times(batch: int, max_scans: int = 1 << 16) -> np.ndarray:
+    """[scans, 3] milliseconds from the launch start to each scan's tiles done
+    and merge done (third column 0), scans in queue order."""
+    out = np.zeros(3 * max_scans, np.float64)
+    n = lib().cvx_batch_phase_times(batch, out.ctypes.data_as(ctypes.c_void_p), max_scans)
     if n < 0:
         raise CovoxError(n, "cvx_batch_phase_times")
     return out[:3 * n].reshape(n, 3)
@@ -290,6 +293,20 @@ def cvx_submap_bounds(handle: int, stream=None) -> np.ndarray:
     check(lib().cvx_submap_bounds(handle, out.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)),
           "cvx_submap_bounds")
     return out
+
+
+def cvx_submap_overlaps(bounds, poses, with_boxes: bool = False, stream=None):
+    """bounds: device float32 [n,6]; poses: device float32 [n,12] (world <-
+    submap).  Returns (volume [n,n], boxes [n,n,6] or None) device tensors."""
+    import torch
+    n = int(bounds.shape[0])
+    vol = torch.empty((n, n), dtype=torch.float32, device=bounds.device)
+    boxes = torch.empty((n, n, 6), dtype=torch.float32, device=bounds.device) if with_boxes else None
+    check(lib().cvx_submap_overlaps(n, _dev_ptr(bounds, "torch.float32", "bounds"),
+                                    _dev_ptr(poses, "torch.float32", "poses"), vol.data_ptr(),
+                                    None if boxes is None else boxes.data_ptr(), _stream_handle(stream)),
+          "cvx_submap_overlaps")
+    return vol, boxes
 
 
 def cvx_block_hash_create(slots: int, max_blocks: int) -> int:
@@ -412,6 +429,14 @@ def cvx_weight_model_infer(model: int, features, weights_out, stream=None):
     check(lib().cvx_weight_model_infer(model, _dev_ptr(features, "torch.float32", "features"), n,
                                        _dev_ptr(weights_out, "torch.float32", "weights"), _stream_handle(stream)),
           "cvx_weight_model_infer")
+
+
+def cvx_weight_model_point_weights(model: int, points, height: int, width: int, sensor: int, max_range: float,
+                                   weights_out, stream=None):
+    check(lib().cvx_weight_model_point_weights(model, _dev_ptr(points, "torch.float32", "points"), int(height),
+                                               int(width), int(sensor), float(max_range),
+                                               _dev_ptr(weights_out, "torch.float32", "weights"),
+                                               _stream_handle(stream)), "cvx_weight_model_point_weights")
 
 
 def cvx_weight_model_train_step(model: int, features, e2, mask, lr: float, stream=None):

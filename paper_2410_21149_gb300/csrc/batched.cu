@@ -2,16 +2,23 @@
 //
 // Scans of one submap are frames in the order given; scans of different
 // submaps are independent (submaps are separate maps, coVoxSLAM Sec. III-C).
-// The host groups the scans into waves (wave k = the k-th scan of every
-// submap that has one) and one cooperative kernel walks the waves:
-//   phase 1  every tile of every scan of the wave: integrate_tile (count,
-//            allocate, per-voxel sums; Sec. III-D), tiles spread over all
-//            CTAs so uneven scans share the GPU (workload equalisation);
-//   phase 2  every touched block of every submap of the wave: merge_span;
-//   phase 3  per-submap bookkeeping of the frame (counters, error words).
-// Phases are separated by grid barriers whose spins are bounded: a barrier
-// that gives up records CVX_ERR_TIMEOUT and every CTA leaves the kernel.
-// The arithmetic is the per-scan path's device code, unchanged.
+// One cooperative kernel works through a queue of items in dependency order,
+// with no grid-wide barrier:
+//   tile item   one tile of one scan: integrate_tile (count, allocate,
+//               per-voxel sums; Sec. III-D) into the scan's per-scan set;
+//   merge item  one of kMergeParts parts of a scan's merge: every
+//               kMergeParts-th span of the submap's allocated blocks, the
+//               blocks stamped with the scan's epoch merged into D and W.
+// An item waits (bounded) only for what it needs: a tile for the merge that
+// last used its per-scan set (pipelined submaps have two sets, so a scan's
+// tiles overlap the previous scan's merge), a merge part for all tiles of its
+// scan and for the merge of the submap's previous scan (D and W in frame
+// order).  Every item waits only on items earlier in the queue, which
+// resident CTAs hold, so the launch always progresses; a wait that runs out
+// records CVX_ERR_TIMEOUT, after which every CTA drains the queue and leaves.
+// Load balance is dynamic (Sec. III-D workload equalisation): each CTA takes
+// the next item as soon as it is free.  The arithmetic is the per-scan path's
+// device code, unchanged.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,31 +36,72 @@ using namespace covox;
 
 namespace {
 
-struct BatchDev {
-  const SubmapDev* maps;   // [n_maps] views, or [2 * n_maps] (parity views) when pipelined
-  const ScanDev* scans;    // [n_scans] in wave order
-  const int* scan_map;     // [n_scans] submap of each scan
-  const int* scan_lb;      // [n_scans] shared block slots
-  const int* tile_prefix;  // [n_scans + 1] tiles before each scan (wave order)
-  const int* wave_begin;   // [n_waves + 1] first scan of each wave
-  int n_waves;
-  int pipelined;           // 1: wave w uses per-scan set w & 1 and merges overlap the next tiles
-  unsigned* bar_count;
-  unsigned* bar_gen;
-  int* err;
-  unsigned long long* phase_ns;   // [n_waves * 3 + 1] globaltimer stamps, or nullptr
-  long long barrier_polls;        // polls before a grid barrier gives up
-  int missing_cta;                // test hook: this CTA leaves before its first arrival (-1: none)
+constexpr int kMergeParts = 32;                  // merge items per scan
+constexpr long long kWaitPolls = 1ll << 21;      // about a second of polling at the sleep below
+constexpr int kMaxBatchMaps = 1024;
+constexpr int kErrIncomplete = 8;                // a scan was left unmerged (only after a timeout)
+
+// Per scan of a launch, in queue order of its tiles.
+struct ScanMeta {
+  int view;       // index into BatchDev::views (2 * submap + per-scan set)
+  int prev;       // previous scan of the same submap (its merge precedes this one's), or -1
+  int prev_set;   // the scan whose merge frees this scan's per-scan set, or -1
+  int n_tiles;
+  int lb;         // shared block slots
+  int epoch_end;  // > 0: the submap's last scan of the launch, st->epoch advances by this much
 };
 
-__device__ __forceinline__ const SubmapDev& view(const BatchDev& b, int map, int wave) {
-  return b.pipelined ? b.maps[2 * map + (wave & 1)] : b.maps[map];
-}
+struct BatchDev {
+  const SubmapDev* views;   // [2 * n_maps]: per submap, per-scan set 0 and 1 (the same when unpipelined)
+  const ScanDev* scans;     // [n_scans]
+  const ScanMeta* meta;     // [n_scans]
+  const int* seg_first;     // [n_segs + 1] first item of each queue segment
+  const int* seg_code;      // [n_segs] scan index, bit 30 set for a merge segment
+  int n_segs;
+  int n_scans;
+  int* ctr;                 // head, err, exit count, spare, then per scan: tiles done, merge tickets, merged flag
+  unsigned long long* phase_ns;   // [1 + 2 * n_scans]: launch start, per scan tiles done / merged
+  long long polls;          // polls before a wait gives up
+  int missing_cta;          // test hook: this CTA takes one item and leaves without doing it (-1: none)
+};
+
+__device__ __forceinline__ int* tiles_done(const BatchDev& b, int s) { return b.ctr + 4 + 3 * s; }
+__device__ __forceinline__ int* merge_ticket(const BatchDev& b, int s) { return b.ctr + 4 + 3 * s + 1; }
+__device__ __forceinline__ int* merged_flag(const BatchDev& b, int s) { return b.ctr + 4 + 3 * s + 2; }
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Thread 0 waits until *addr >= target (bounded; gives up at once when the
+// launch has failed), then the CTA goes on.  The fence after the wait orders
+// the CTA's later reads after the producer's writes, which it published with
+// a fence before its counter update.
+__device__ bool wait_at_least(const BatchDev& b, const int* addr, int target, int* ok_smem) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    long long it = 0;
+    while (*((volatile const int*)addr) < target) {
+      if (*((volatile int*)(b.ctr + 1)) != 0) {
+        ok = 0;
+        break;
+      }
+      if (++it > b.polls) {
+        atomicOr(b.ctr + 1, kErrTimeout);
+        ok = 0;
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+    *ok_smem = ok;
+  }
+  __syncthreads();
+  const int ok = *ok_smem;
+  __syncthreads();
+  return ok != 0;
 }
 
 // Sum of one value over the 256-thread CTA (thread 0 gets it).
@@ -69,195 +117,117 @@ __device__ __forceinline__ unsigned long long cta_sum_b(unsigned long long v, un
   return t;
 }
 
-__device__ __forceinline__ void stamp(const BatchDev& b, int slot) {
-  if (b.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) b.phase_ns[slot] = global_ns();
-}
-
-constexpr long long kBarrierSpin = 1ll << 24;   // ~1 s at the sleep below
-constexpr int kMaxWaveScans = 1024;
-
-__device__ bool grid_barrier(const BatchDev& b) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    const unsigned g = *((volatile unsigned*)b.bar_gen);
-    __threadfence();
-    if (atomicAdd(b.bar_count, 1u) == gridDim.x - 1) {
-      *((volatile unsigned*)b.bar_count) = 0;
-      __threadfence();
-      atomicAdd(b.bar_gen, 1u);
-    } else {
-      long long it = 0;
-      while (*((volatile unsigned*)b.bar_gen) == g) {
-        if (++it > b.barrier_polls || *((volatile int*)b.err) != 0) {
-          atomicOr(b.err, kErrTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
+// Merge part `part` of scan s: spans part, part + kMergeParts, ... of the
+// submap's allocated blocks (blocks the submap's next scan allocates
+// meanwhile carry other epochs, so any count read now covers this scan's).
+__device__ void merge_part(const BatchDev& b, int s, int part, SpanList* sl, unsigned long long* red) {
+  const SubmapDev& m = b.views[b.meta[s].view];
+  const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
+  const bool skip = *((volatile int32_t*)m.frame_err) != 0;
+  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u + b.scans[s].epoch_add;
+  unsigned long long merged = 0, touched = 0;
+  for (int span = part; span * kSpanBlocks < nb; span += kMergeParts) {
+    int t = 0;
+    merged += merge_span(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl, &t);
+    touched += t;
   }
-  __syncthreads();
-  return ok != 0;
+  const unsigned long long c = cta_sum_b(merged, red);
+  if (threadIdx.x == 0) {
+    if (c) atomicAdd(&m.st->voxels_merged, c);
+    if (touched) atomicAdd(&m.st->blocks_touched, touched);
+  }
 }
 
-__device__ __forceinline__ int find_scan(const int* prefix, int lo, int hi, int g) {
-  // largest s in [lo, hi) with prefix[s] <= g
+// Frame bookkeeping of scan s, by the CTA finishing its last merge part.
+__device__ void close_scan(const BatchDev& b, int s) {
+  const ScanMeta& sm = b.meta[s];
+  const SubmapDev& m = b.views[sm.view];
+  State* st = m.st;
+  st->frames += 1;
+  st->sticky_err |= *((volatile int32_t*)m.frame_err);
+  *m.frame_err = 0;
+  if (sm.epoch_end > 0) st->epoch += (uint32_t)sm.epoch_end;   // after the submap's last scan of the launch
+}
+
+// The queue segment holding item it (read-only descriptors: through the
+// non-coherent cache).
+__device__ __forceinline__ int find_segment(const BatchDev& b, int it) {
+  int lo = 0, hi = b.n_segs;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (prefix[mid] <= g) lo = mid; else hi = mid;
+    if (__ldg(b.seg_first + mid) <= it) lo = mid; else hi = mid;
   }
   return lo;
 }
 
-// Blocks a merge of wave w covers: the submap's allocated blocks -- with
-// pipelined waves as they stood when the wave's tiles had finished (the next
-// wave's tiles allocate meanwhile; every CTA must see the same count, since
-// the spans of all the wave's submaps are numbered together).
-__device__ __forceinline__ int wave_blocks(const BatchDev& b, const SubmapDev& m, int w) {
-  const int nb = b.pipelined ? *((volatile int32_t*)((w & 1) ? &m.st->nb_closed1 : &m.st->nb_closed0))
-                             : *((volatile int32_t*)&m.st->n_blocks);
-  return min(nb, m.max_blocks);
-}
-
-// Merge work of wave w: the allocated blocks of every submap of the wave in
-// spans of kSpanBlocks consecutive pool indices (a span never crosses
-// submaps; span_prefix counts them per scan of the wave).  In each span the
-// blocks stamped with the scan's epoch are compacted and merged (merge_span).
-// Spans first, first + step, ... (single: only the first).
-__device__ void merge_wave(const BatchDev& b, int w, const int* span_prefix, int first, int step, bool single,
-                           SpanList* sl, unsigned long long* red) {
-  const int s0 = b.wave_begin[w], ns = b.wave_begin[w + 1] - s0;
-  const int total = span_prefix[ns];
-  for (int span = first; span < total; span += step) {
-    const int q = find_scan(span_prefix, 0, ns, span);
-    const SubmapDev& m = view(b, b.scan_map[s0 + q], w);
-    const int nb = wave_blocks(b, m, w);
-    const int p0 = (span - span_prefix[q]) * kSpanBlocks;
-    const bool skip = *((volatile int32_t*)m.frame_err) != 0;
-    // the scan's epoch: its tiles ran with st->epoch + 1; pipelined waves have
-    // advanced st->epoch past them before their merges
-    const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + (b.pipelined ? 0u : 1u);
-    int t = 0;
-    const int merged = merge_span(m, p0, min(kSpanBlocks, nb - p0), ep, skip, sl, &t);
-    const unsigned long long c = cta_sum_b(merged, red);
-    if (threadIdx.x == 0) {
-      if (c) atomicAdd(&m.st->voxels_merged, c);
-      if (t) atomicAdd(&m.st->blocks_touched, (unsigned long long)t);
-    }
-    if (single) break;
-  }
-}
-
-// spans of wave w's scans (thread 0), prefix sums in span_prefix
-__device__ void wave_spans(const BatchDev& b, int w, int* span_prefix) {
-  if (threadIdx.x == 0) {
-    const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
-    int acc = 0;
-    for (int s = s0; s < s1; ++s) {
-      span_prefix[s - s0] = acc;
-      const SubmapDev& m = view(b, b.scan_map[s], w);
-      acc += (wave_blocks(b, m, w) + kSpanBlocks - 1) / kSpanBlocks;
-    }
-    span_prefix[s1 - s0] = acc;
-  }
-  __syncthreads();
-}
-
-// per-submap bookkeeping of wave w's frames (CTA 0)
-__device__ void wave_bookkeeping(const BatchDev& b, int w) {
-  if (blockIdx.x != 0) return;
-  const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
-  for (int s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-    const SubmapDev& m = view(b, b.scan_map[s], w);
-    State* st = m.st;
-    st->frames += 1;
-    st->sticky_err |= *m.frame_err;
-    *m.frame_err = 0;
-    if (!b.pipelined) st->epoch += 1;   // the submap's next scan takes the next epoch
-  }
-}
-
-// pipelined: the tiles of wave w are done, so their submaps' next scans take
-// the next epoch (CTA 0, after the step's barrier)
-__device__ void wave_epoch(const BatchDev& b, int w) {
-  if (blockIdx.x != 0) return;
-  for (int s = b.wave_begin[w] + threadIdx.x; s < b.wave_begin[w + 1]; s += blockDim.x) {
-    State* st = view(b, b.scan_map[s], w).st;
-    if (w & 1) st->nb_closed1 = st->n_blocks;
-    else st->nb_closed0 = st->n_blocks;
-    st->epoch += 1;
-  }
-}
-
 template <int kVariant>
-__global__ void __launch_bounds__(kTileThreads, 4) batched_kernel(BatchDev b) {
+__global__ void __launch_bounds__(kTileThreads, 3) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ int span_prefix[kMaxWaveScans + 1];
+  __shared__ int item_smem[3];
+  __shared__ int ok_smem;
   __shared__ SpanList span;
   __shared__ unsigned long long red[kTileThreads / 32];
-  if ((int)blockIdx.x == b.missing_cta) return;   // test hook: never arrives at a barrier
-  stamp(b, 0);
-  if (!b.pipelined) {
-    for (int w = 0; w < b.n_waves; ++w) {
-      const int s0 = b.wave_begin[w], s1 = b.wave_begin[w + 1];
-      // phase 1: tiles of all scans of the wave
-      const int t0 = b.tile_prefix[s0], total = b.tile_prefix[s1] - t0;
-      for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        const int s = find_scan(b.tile_prefix, s0, s1, t0 + t);
-        integrate_tile_v<kVariant>(view(b, b.scan_map[s], w), b.scans[s], t0 + t - b.tile_prefix[s], smem,
-                                   b.scan_lb[s]);
-      }
-      if (!grid_barrier(b)) return;
-      stamp(b, 3 * w + 1);
-      // phase 2: merge every touched block of every submap of the wave
-      wave_spans(b, w, span_prefix);
-      merge_wave(b, w, span_prefix, blockIdx.x, gridDim.x, false, &span, red);
-      if (!grid_barrier(b)) return;
-      stamp(b, 3 * w + 2);
-      // phase 3: per-submap bookkeeping of this frame
-      wave_bookkeeping(b, w);
-      if (!grid_barrier(b)) return;
-      stamp(b, 3 * w + 3);
+  if (b.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) b.phase_ns[0] = global_ns();
+  const int n_items = __ldg(b.seg_first + b.n_segs);
+  // dependencies this CTA has already seen satisfied (counters only grow)
+  int seen_merged = -1, seen_tiles = -1;
+  for (bool first = true;; first = false) {
+    if (threadIdx.x == 0) {
+      const int it = *((volatile int*)(b.ctr + 1)) != 0 ? n_items : atomicAdd(b.ctr, 1);
+      item_smem[0] = it;
+      item_smem[1] = it < n_items ? find_segment(b, it) : -1;
     }
-    return;
+    __syncthreads();
+    const int it = item_smem[0], seg = item_smem[1];
+    __syncthreads();
+    if (it >= n_items) break;
+    if (first && (int)blockIdx.x == b.missing_cta) break;   // test hook: the item is never done
+    const int code = __ldg(b.seg_code + seg);
+    const int s = code & 0x3fffffff;
+    const int part = it - __ldg(b.seg_first + seg);
+    const ScanMeta sm = b.meta[s];
+    if (!(code & (1 << 30))) {   // tile item
+      if (sm.prev_set >= 0 && sm.prev_set != seen_merged) {
+        if (!wait_at_least(b, merged_flag(b, sm.prev_set), 1, &ok_smem)) continue;
+        seen_merged = sm.prev_set;
+      }
+      integrate_tile_v<kVariant>(b.views[sm.view], b.scans[s], part, smem, sm.lb);
+      if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(tiles_done(b, s), 1) == sm.n_tiles - 1 && b.phase_ns) b.phase_ns[1 + 2 * s] = global_ns();
+      }
+    } else {                     // merge item
+      if (s != seen_tiles) {
+        if (!wait_at_least(b, tiles_done(b, s), sm.n_tiles, &ok_smem)) continue;
+        seen_tiles = s;
+      }
+      if (sm.prev >= 0 && sm.prev != seen_merged) {
+        if (!wait_at_least(b, merged_flag(b, sm.prev), 1, &ok_smem)) continue;
+        seen_merged = sm.prev;
+      }
+      merge_part(b, s, part, &span, red);
+      if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(merge_ticket(b, s), 1) == kMergeParts - 1) {
+          close_scan(b, s);
+          if (b.phase_ns) b.phase_ns[2 + 2 * s] = global_ns();
+          __threadfence();
+          atomicExch(merged_flag(b, s), 1);
+        }
+      }
+      __syncthreads();
+    }
   }
-  // pipelined: step w runs the tiles of wave w and the merges of wave w - 1
-  // (different per-scan sets; tiles never read D or W), then the bookkeeping
-  // of wave w - 1 frees its set for wave w + 1.
-  for (int w = 0; w <= b.n_waves; ++w) {
-    int n_tiles = 0, t0 = 0, s0 = 0, s1 = 0;
-    if (w < b.n_waves) {
-      s0 = b.wave_begin[w];
-      s1 = b.wave_begin[w + 1];
-      t0 = b.tile_prefix[s0];
-      n_tiles = b.tile_prefix[s1] - t0;
+  // the last CTA to leave checks that every scan was merged
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(b.ctr + 2, 1) == gridDim.x - 1) {
+      for (int s = 0; s < b.n_scans; ++s)
+        if (*((volatile int*)merged_flag(b, s)) == 0) {
+          atomicOr(b.ctr + 1, kErrIncomplete);
+          break;
+        }
     }
-    int n_spans = 0;
-    if (w > 0) {
-      wave_spans(b, w - 1, span_prefix);
-      n_spans = span_prefix[b.wave_begin[w] - b.wave_begin[w - 1]];   // merge spans
-    }
-    const int items = n_tiles + n_spans;
-    for (int it = blockIdx.x; it < items; it += gridDim.x) {
-      if (it < n_tiles) {
-        const int s = find_scan(b.tile_prefix, s0, s1, t0 + it);
-        integrate_tile_v<kVariant>(view(b, b.scan_map[s], w), b.scans[s], t0 + it - b.tile_prefix[s], smem,
-                                   b.scan_lb[s]);
-      } else {
-        merge_wave(b, w - 1, span_prefix, it - n_tiles, 1, true, &span, red);   // one item: a span
-      }
-    }
-    if (!grid_barrier(b)) return;
-    stamp(b, 3 * w + 1);
-    if (w > 0) wave_bookkeeping(b, w - 1);
-    if (w < b.n_waves) wave_epoch(b, w);
-    if (!grid_barrier(b)) return;
-    stamp(b, 3 * w + 2);
-    stamp(b, 3 * w + 3);
   }
 }
 
@@ -272,17 +242,16 @@ struct cvx_batch {
   void* dev;          // descriptor block on the device
   void* host;         // pinned staging of the same layout
   size_t bytes;
-  unsigned* bar;      // count, gen, err (device)
+  int* ctr;           // launch counters (device)
   cudaEvent_t copied; // host staging reusable once the previous upload ran
   bool pending;
-  int grid;           // persistent grid size (CTAs)
   int lb_max;
-  unsigned long long* phase_ns;   // [3 * max_scans + 1] when phase timing is on
+  unsigned long long* phase_ns;   // [1 + 2 * max_scans] when timing is on
   bool timing;
-  int last_waves;
-  int wave_limit;     // most scans per wave (0: no limit)
+  int last_scans;
+  int wave_limit;     // most scans per round of the queue (0: no limit)
   int missing_cta;    // test hook (-1: off)
-  long long barrier_polls;
+  long long polls;
 };
 
 namespace {
@@ -290,34 +259,34 @@ namespace {
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 struct Layout {
-  size_t maps, scans, scan_map, scan_lb, tile_prefix, wave_begin, total;
+  size_t views, scans, meta, seg_first, seg_code, total;
 };
 
 Layout layout(int max_maps, int max_scans) {
   Layout L;
   size_t o = 0;
-  L.maps = o;
+  L.views = o;
   o = align16(o + sizeof(SubmapDev) * 2 * max_maps);
   L.scans = o;
   o = align16(o + sizeof(ScanDev) * max_scans);
-  L.scan_map = o;
-  o = align16(o + sizeof(int) * max_scans);
-  L.scan_lb = o;
-  o = align16(o + sizeof(int) * max_scans);
-  L.tile_prefix = o;
-  o = align16(o + sizeof(int) * (max_scans + 1));
-  L.wave_begin = o;
-  o = align16(o + sizeof(int) * (max_scans + 1));
+  L.meta = o;
+  o = align16(o + sizeof(ScanMeta) * max_scans);
+  L.seg_first = o;
+  o = align16(o + sizeof(int) * (2 * (size_t)max_scans + 1));
+  L.seg_code = o;
+  o = align16(o + sizeof(int) * 2 * (size_t)max_scans);
   L.total = o;
   return L;
 }
+
+size_t counter_bytes(int n_scans) { return sizeof(int) * (4 + 3 * (size_t)n_scans); }
 
 }  // namespace
 
 extern "C" {
 
 cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** out) {
-  if (!out || max_submaps <= 0 || max_scans <= 0 || max_submaps > kMaxWaveScans || max_scans > (1 << 20))
+  if (!out || max_submaps <= 0 || max_scans <= 0 || max_submaps > kMaxBatchMaps || max_scans > (1 << 20))
     return CVX_ERR_INVALID_ARG;
   *out = nullptr;
   cvx_batch* b = new (std::nothrow) cvx_batch();
@@ -326,38 +295,29 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
   b->max_scans = max_scans;
   const Layout L = layout(max_submaps, max_scans);
   b->bytes = L.total;
+  b->lb_max = kMaxLocalBlocks;
+  b->missing_cta = -1;
+  b->polls = kWaitPolls;
   if (cudaMalloc(&b->dev, L.total) != cudaSuccess || cudaMallocHost(&b->host, L.total) != cudaSuccess ||
-      cudaMalloc((void**)&b->bar, 16) != cudaSuccess || cudaMemset(b->bar, 0, 16) != cudaSuccess ||
+      cudaMalloc((void**)&b->ctr, counter_bytes(max_scans)) != cudaSuccess ||
+      cudaMalloc((void**)&b->phase_ns, sizeof(unsigned long long) * (1 + 2 * (size_t)max_scans)) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     if (b->dev) cudaFree(b->dev);
     if (b->host) cudaFreeHost(b->host);
-    if (b->bar) cudaFree(b->bar);
+    if (b->ctr) cudaFree(b->ctr);
+    if (b->phase_ns) cudaFree(b->phase_ns);
     delete b;
     return CVX_ERR_OOM;
   }
-  b->lb_max = kMaxLocalBlocks;
-  b->missing_cta = -1;
-  b->barrier_polls = kBarrierSpin;
-  if (cudaMalloc((void**)&b->phase_ns, sizeof(unsigned long long) * (3 * (size_t)max_scans + 8)) != cudaSuccess) {
+  if (cudaMemset(b->ctr, 0, counter_bytes(max_scans)) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(b->dev);
-    cudaFreeHost(b->host);
-    cudaFree(b->bar);
-    delete b;
-    return CVX_ERR_OOM;
+    cvx_batch_destroy(b);
+    return CVX_ERR_CUDA;
   }
   for (int v = 0; v < 7; ++v)
     cudaFuncSetAttribute((const void*)kBatched[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tile_smem_bytes(kMaxLocalBlocks));
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kBatched[0], kTileThreads,
-                                                    tile_smem_bytes(kDefaultLocalBlocks)) != cudaSuccess ||
-      per_sm <= 0) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  b->grid = per_sm * num_sms();
   *out = b;
   return CVX_OK;
 }
@@ -367,7 +327,7 @@ void cvx_batch_destroy(cvx_batch* b) {
   cudaEventSynchronize(b->copied);
   cudaFree(b->dev);
   cudaFreeHost(b->host);
-  cudaFree(b->bar);
+  cudaFree(b->ctr);
   cudaFree(b->phase_ns);
   cudaEventDestroy(b->copied);
   delete b;
@@ -382,7 +342,7 @@ cvx_status cvx_batch_wave_limit(cvx_batch* b, int32_t max_scans_per_wave) {
 cvx_status cvx_batch_test_missing_cta(cvx_batch* b, int32_t missing_cta, int64_t barrier_polls) {
   if (!b) return CVX_ERR_INVALID_ARG;
   b->missing_cta = missing_cta < 0 ? -1 : missing_cta;
-  b->barrier_polls = (missing_cta >= 0 && barrier_polls > 0) ? barrier_polls : kBarrierSpin;
+  b->polls = (missing_cta >= 0 && barrier_polls > 0) ? barrier_polls : kWaitPolls;
   return CVX_OK;
 }
 
@@ -392,22 +352,22 @@ cvx_status cvx_batch_timing(cvx_batch* b, int32_t enable) {
   return CVX_OK;
 }
 
-int32_t cvx_batch_phase_times(cvx_batch* b, double* ms, int32_t max_waves) {
-  if (!b || !ms || max_waves <= 0) return CVX_ERR_INVALID_ARG;
-  const int nw = b->last_waves < max_waves ? b->last_waves : max_waves;
-  if (nw <= 0) return 0;
-  unsigned long long* t = new (std::nothrow) unsigned long long[3 * (size_t)nw + 1];
-  if (!t) return CVX_ERR_OOM;
-  if (cudaMemcpy(t, b->phase_ns, sizeof(unsigned long long) * (3 * (size_t)nw + 1), cudaMemcpyDeviceToHost) !=
+int32_t cvx_batch_phase_times(cvx_batch* b, double* ms, int32_t max_scans) {
+  if (!b || !ms || max_scans <= 0) return CVX_ERR_INVALID_ARG;
+  const int ns = b->last_scans < max_scans ? b->last_scans : max_scans;
+  if (ns <= 0) return 0;
+  std::vector<unsigned long long> t(1 + 2 * (size_t)ns);
+  if (cudaMemcpy(t.data(), b->phase_ns, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost) !=
       cudaSuccess) {
     cudaGetLastError();
-    delete[] t;
     return CVX_ERR_CUDA;
   }
-  for (int w = 0; w < nw; ++w)
-    for (int p = 0; p < 3; ++p) ms[3 * w + p] = (double)(t[3 * w + p + 1] - t[3 * w + p]) * 1e-6;
-  delete[] t;
-  return nw;
+  for (int s = 0; s < ns; ++s) {
+    ms[3 * s] = (double)(t[1 + 2 * s] - t[0]) * 1e-6;
+    ms[3 * s + 1] = (double)(t[2 + 2 * s] - t[0]) * 1e-6;
+    ms[3 * s + 2] = 0.0;
+  }
+  return ns;
 }
 
 cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_maps,
@@ -418,11 +378,11 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   for (int q = 0; q < n_maps; ++q)
     for (int r = 0; r < q; ++r)
       if (!maps[q] || maps[q] == maps[r]) return CVX_ERR_INVALID_ARG;   // distinct submaps
-  // validate and describe every scan; empty scans are no frames; group the
-  // rest into waves (wave k = k-th non-empty scan of each submap)
+  // validate and describe every scan; empty scans are no frames; the rank of
+  // a scan is its frame number within its submap in this launch
   std::vector<ScanDev> sd(n_scans);
   std::vector<int> lbs(n_scans), rank(n_scans), per_map(n_maps, 0), order;
-  int n_waves = 0, lb_max = 0;
+  int lb_max = 0;
   for (int s = 0; s < n_scans; ++s) {
     const cvx_scan_desc& d = scans[s];
     if (d.submap < 0 || d.submap >= n_maps) return CVX_ERR_INVALID_ARG;
@@ -435,23 +395,24 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     order.push_back(s);
   }
   if (order.empty()) return CVX_OK;
+  // queue order: rounds of scans of equal rank (cut into chunks of at most
+  // wave_limit scans); the merges of a round's scans follow in the next round
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return rank[a] < rank[c]; });
   const int n_run = (int)order.size();
-  // waves: the k-th scans of all submaps, cut into chunks of at most
-  // wave_limit scans (chunks of one rank are independent of each other)
+  std::vector<int> round_of(n_run);
+  int n_rounds = 0;
   {
-    int w = -1, prev = -1, in_wave = 0;
+    int prev = -1, in_round = 0;
     for (int k = 0; k < n_run; ++k) {
       const int rk = rank[order[k]];
-      if (rk != prev || (b->wave_limit > 0 && in_wave >= b->wave_limit)) {
-        ++w;
-        in_wave = 0;
+      if (rk != prev || (b->wave_limit > 0 && in_round >= b->wave_limit)) {
+        ++n_rounds;
+        in_round = 0;
         prev = rk;
       }
-      rank[order[k]] = w;   // from here on: the wave index
-      ++in_wave;
+      round_of[k] = n_rounds - 1;
+      ++in_round;
     }
-    n_waves = w + 1;
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -470,34 +431,61 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   }
   const Layout L = layout(b->max_maps, b->max_scans);
   char* h = (char*)b->host;
-  SubmapDev* hm = (SubmapDev*)(h + L.maps);
+  SubmapDev* hv = (SubmapDev*)(h + L.views);
   ScanDev* hs = (ScanDev*)(h + L.scans);
-  int* hmap = (int*)(h + L.scan_map);
-  int* hlb = (int*)(h + L.scan_lb);
-  int* htp = (int*)(h + L.tile_prefix);
-  int* hwb = (int*)(h + L.wave_begin);
-  bool pipelined = true;
-  for (int q = 0; q < n_maps; ++q) pipelined = pipelined && maps[q]->pipelined;
+  ScanMeta* hm = (ScanMeta*)(h + L.meta);
+  int* hsf = (int*)(h + L.seg_first);
+  int* hsc = (int*)(h + L.seg_code);
   for (int q = 0; q < n_maps; ++q) {
-    if (pipelined) {
-      hm[2 * q] = maps[q]->dev;
-      hm[2 * q + 1] = maps[q]->dev_b;
-    } else {
-      hm[q] = maps[q]->dev;
-    }
+    hv[2 * q] = maps[q]->dev;
+    hv[2 * q + 1] = maps[q]->pipelined ? maps[q]->dev_b : maps[q]->dev;
   }
-  int tiles = 0, wave = -1;
+  // per scan (in queue order): descriptor, set, dependencies
+  std::vector<int> last_of_map(n_maps, -1), last2_of_map(n_maps, -1);
   for (int k = 0; k < n_run; ++k) {
     const int s = order[k];
-    while (wave < rank[s]) hwb[++wave] = k;
+    const int q = scans[s].submap;
+    const bool two = maps[q]->pipelined;
     hs[k] = sd[s];
-    hmap[k] = scans[s].submap;
-    hlb[k] = lbs[s];
-    htp[k] = tiles;
-    tiles += sd[s].n_tiles;
+    hs[k].epoch_add = (uint32_t)rank[s];
+    ScanMeta& mt = hm[k];
+    mt.view = 2 * q + (two ? (rank[s] & 1) : 0);
+    mt.prev = last_of_map[q];
+    mt.prev_set = two ? last2_of_map[q] : last_of_map[q];
+    mt.n_tiles = sd[s].n_tiles;
+    mt.lb = lbs[s];
+    mt.epoch_end = rank[s] == per_map[q] - 1 ? per_map[q] : 0;
+    last2_of_map[q] = last_of_map[q];
+    last_of_map[q] = k;
   }
-  htp[n_run] = tiles;
-  hwb[n_waves] = n_run;
+  // queue segments, round by round: merges of the previous round's
+  // single-set scans (their submaps' next tiles wait for them), this round's
+  // tiles, then the merges of the previous round's two-set scans (the next
+  // tiles of those submaps do not wait for them)
+  int n_segs = 0, items = 0;
+  auto add_seg = [&](int code, int n) {
+    hsf[n_segs] = items;
+    hsc[n_segs] = code;
+    ++n_segs;
+    items += n;
+  };
+  {
+    int k0 = 0;
+    int pk0 = 0, pk1 = 0;   // previous round's scans [pk0, pk1)
+    for (int r = 0; r <= n_rounds; ++r) {
+      int k1 = k0;
+      while (k1 < n_run && round_of[k1] == r) ++k1;
+      for (int k = pk0; k < pk1; ++k)
+        if (!maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), kMergeParts);
+      for (int k = k0; k < k1; ++k) add_seg(k, hm[k].n_tiles);
+      for (int k = pk0; k < pk1; ++k)
+        if (maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), kMergeParts);
+      pk0 = k0;
+      pk1 = k1;
+      k0 = k1;
+    }
+  }
+  hsf[n_segs] = items;
   if (cudaMemcpyAsync(b->dev, b->host, L.total, cudaMemcpyHostToDevice, st) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
@@ -514,27 +502,24 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     // a scan left pending by the pipelined per-scan path is merged first
     if (flush_pending(maps[q], st, false) != CVX_OK) return CVX_ERR_CUDA;
   }
-  char* d = (char*)b->dev;
-  BatchDev bd;
-  bd.maps = (const SubmapDev*)(d + L.maps);
-  bd.scans = (const ScanDev*)(d + L.scans);
-  bd.scan_map = (const int*)(d + L.scan_map);
-  bd.scan_lb = (const int*)(d + L.scan_lb);
-  bd.tile_prefix = (const int*)(d + L.tile_prefix);
-  bd.wave_begin = (const int*)(d + L.wave_begin);
-  bd.n_waves = n_waves;
-  bd.pipelined = pipelined ? 1 : 0;
-  bd.bar_count = b->bar;
-  bd.bar_gen = b->bar + 1;
-  bd.err = (int*)(b->bar + 2);
-  bd.phase_ns = b->timing ? b->phase_ns : nullptr;
-  bd.barrier_polls = b->barrier_polls;
-  bd.missing_cta = b->missing_cta;
-  b->last_waves = pipelined ? n_waves + 1 : n_waves;   // pipelined: steps (tiles of w + merges of w - 1)
-  if (cudaMemsetAsync(b->bar, 0, 16, st) != cudaSuccess) {
+  if (cudaMemsetAsync(b->ctr, 0, counter_bytes(n_run), st) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
+  char* d = (char*)b->dev;
+  BatchDev bd;
+  bd.views = (const SubmapDev*)(d + L.views);
+  bd.scans = (const ScanDev*)(d + L.scans);
+  bd.meta = (const ScanMeta*)(d + L.meta);
+  bd.seg_first = (const int*)(d + L.seg_first);
+  bd.seg_code = (const int*)(d + L.seg_code);
+  bd.n_segs = n_segs;
+  bd.n_scans = n_run;
+  bd.ctr = b->ctr;
+  bd.phase_ns = b->timing ? b->phase_ns : nullptr;
+  bd.polls = b->polls;
+  bd.missing_cta = b->missing_cta;
+  b->last_scans = n_run;
   // one variant for every scan: a kernel holding only that code
   int variant = -2;
   for (int k = 0; k < n_run; ++k) {
@@ -549,7 +534,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
-  const int grid = per_sm * num_sms();
+  const int grid = std::min(per_sm * num_sms(), std::max(items, 1));
   void* args[] = {&bd};
   cudaError_t e;
   COVOX_LAUNCH(kKBatched, st,
@@ -564,12 +549,12 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
 
 int32_t cvx_batch_error(cvx_batch* b) {
   if (!b) return CVX_ERR_INVALID_ARG;
-  unsigned v[3] = {0, 0, 0};
-  if (cudaMemcpy(v, b->bar, 12, cudaMemcpyDeviceToHost) != cudaSuccess) {
+  int v[2] = {0, 0};
+  if (cudaMemcpy(v, b->ctr, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
-  return (v[2] & kErrTimeout) ? CVX_ERR_TIMEOUT : CVX_OK;
+  return (v[1] & (kErrTimeout | kErrIncomplete)) ? CVX_ERR_TIMEOUT : CVX_OK;
 }
 
 }  // extern "C"

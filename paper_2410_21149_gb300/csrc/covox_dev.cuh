@@ -61,6 +61,7 @@ struct ScanDev {
   int32_t weight_mode, dropoff, sensor, organised;
   int32_t carve;         // traverse from the sensor origin (free-space carving)
   int32_t long_band;     // a band may cross more than 512 cells per axis (trunc > 250 voxels)
+  uint32_t epoch_add;    // the scan's epoch is st->epoch + 1 + epoch_add (its rank in a batched launch)
   int32_t height, width, tile_w, tile_h, tiles_x, n_tiles;
 };
 

@@ -396,3 +396,60 @@ extern "C" cvx_status cvx_submap_bounds(cvx_submap* map, float lo_hi[6], void* s
   }
   return CVX_OK;
 }
+
+// ------------------------------------------------------------- submap overlap
+// World-frame boxes of two posed submaps and their intersection (the AABB
+// overlap test of the backend, Sec. III-F): each submap's block-corner box
+// (cvx_submap_bounds, submap frame) is carried to the world frame by its pose
+// (world <- submap, 3x4 row-major), the axis-aligned box of its 8 corners
+// taken, and the two boxes intersected.  One thread per ordered pair.
+__device__ __forceinline__ void world_box(const float* b, const float* T, float lo[3], float hi[3]) {
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = 3.40282347e38f;
+    hi[k] = -3.40282347e38f;
+  }
+  for (int c = 0; c < 8; ++c) {
+    const float x = (c & 1) ? b[3] : b[0], y = (c & 2) ? b[4] : b[1], z = (c & 4) ? b[5] : b[2];
+    for (int k = 0; k < 3; ++k) {
+      const float w = T[4 * k] * x + T[4 * k + 1] * y + T[4 * k + 2] * z + T[4 * k + 3];
+      lo[k] = fminf(lo[k], w);
+      hi[k] = fmaxf(hi[k], w);
+    }
+  }
+}
+
+__global__ void overlap_kernel(int n, const float* __restrict__ bounds, const float* __restrict__ poses,
+                               float* __restrict__ volume, float* __restrict__ boxes) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)n * n) return;
+  const int i = (int)(q / n), j = (int)(q % n);
+  const float* bi = bounds + 6 * i;
+  const float* bj = bounds + 6 * j;
+  const bool empty = bi[0] > bi[3] || bi[1] > bi[4] || bi[2] > bi[5] || bj[0] > bj[3] || bj[1] > bj[4] || bj[2] > bj[5];
+  float li[3], hi_[3], lj[3], hj[3], lo[3], hi[3];
+  world_box(bi, poses + 12 * i, li, hi_);
+  world_box(bj, poses + 12 * j, lj, hj);
+  float v = empty ? 0.0f : 1.0f;
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = fmaxf(li[k], lj[k]);
+    hi[k] = fminf(hi_[k], hj[k]);
+    v *= fmaxf(hi[k] - lo[k], 0.0f);
+  }
+  volume[q] = v;
+  if (boxes)
+    for (int k = 0; k < 3; ++k) {
+      boxes[6 * q + k] = lo[k];
+      boxes[6 * q + 3 + k] = hi[k];
+    }
+}
+
+extern "C" cvx_status cvx_submap_overlaps(int32_t n, const float* bounds, const float* poses, float* volume,
+                                          float* boxes, void* stream) {
+  if (n <= 0 || n > 65536 || !bounds || !poses || !volume) return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long pairs = (long long)n * n;
+  COVOX_LAUNCH(kKEsdf, s, overlap_kernel<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(n, bounds, poses, volume,
+                                                                                         boxes));
+  return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
+}
+

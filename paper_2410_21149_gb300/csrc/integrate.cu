@@ -106,8 +106,10 @@ __global__ void __launch_bounds__(kTileThreads) merge_kernel(SubmapDev m) {
 }
 
 // Clear the per-scan sums a launch that gave up left unmerged: the blocks of
-// either per-scan set stamped with the last or the running scan's epoch
-// (reset; merged blocks hold zero sums, so this only repeats their zeroing).
+// either per-scan set stamped with an epoch after the last closed one (a
+// batched launch numbers its scans st->epoch + 1, + 2, ... and closes them
+// all at its end; a pending pipelined scan was dropped before this runs).
+// Reset only: merged blocks hold zero sums, so this at most repeats zeroing.
 __global__ void discard_sums_kernel(SubmapDev a, SubmapDev b, int two_sets) {
   const int nb = min(a.st->n_blocks, a.max_blocks);
   const uint32_t e = a.st->epoch;
@@ -115,7 +117,7 @@ __global__ void discard_sums_kernel(SubmapDev a, SubmapDev b, int two_sets) {
     const SubmapDev& m = set ? b : a;
     for (int p = blockIdx.x; p < nb; p += gridDim.x) {
       const uint32_t t = m.tepoch[p];
-      if (t != e && t != e + 1u) continue;
+      if (t <= e) continue;
       float4* acc = reinterpret_cast<float4*>(m.acc + (size_t)p * kVoxPerBlock);
       for (int q = threadIdx.x; q < kVoxPerBlock / 2; q += blockDim.x) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }

@@ -158,7 +158,6 @@ __device__ __forceinline__ uint32_t slot_hash(unsigned long long key) {
 
 constexpr int kCache = 256;         // block -> pool cache entries per CTA (power of two)
 constexpr int kCachePending = -2;
-constexpr int kCacheWait = 4096;    // polls of a pending cache entry before activating anyway
 
 // The per-scan sums of a voxel are (sum w (d - trunc), sum w): distances are
 // summed relative to +trunc, so the many observations of free space (d
@@ -254,35 +253,27 @@ __device__ __forceinline__ float fixed_value(unsigned lo, int hi, int S, float i
 }
 
 // Pool index of a block through the CTA's block -> pool cache.  The first
-// thread to meet a block activates it and publishes the index; a thread that
-// finds the entry pending waits for it (bounded, then activates the block
-// itself: activation is idempotent).
+// thread to claim an entry looks the block up in the global hash and
+// publishes the answer there; a thread that finds the entry still pending
+// does not wait for it but looks the block up itself (a lookup of an existing
+// block is one read of its hash slot and a store of the same touch epoch;
+// two threads inserting one key are ordered by the key's CAS).
 __device__ __forceinline__ int cached_pool(const SubmapDev& m, const TileSmem& t, unsigned long long key,
                                            uint32_t ep) {
   const uint32_t h = slot_hash(key) >> 24;
   for (int p = 0; p < 8; ++p) {
     const int q = (h + p) & (kCache - 1);
     unsigned long long cur = *((volatile unsigned long long*)(t.ckey + q));
-    bool own = false;
     if (cur == kEmptyKey) {
       cur = atomicCAS(t.ckey + q, kEmptyKey, key);
-      own = cur == kEmptyKey;
-    }
-    if (own) {
-      const int pool = global_activate(m, key, ep);
-      atomicExch(t.cpool + q, pool);
-      return pool;
+      if (cur == kEmptyKey) {
+        const int pool = global_activate(m, key, ep);
+        atomicExch(t.cpool + q, pool);
+        return pool;
+      }
     }
     if (cur == key) {
-      // Another thread of the CTA is activating the block: wait for its
-      // answer in shared memory (a few hundred cycles) rather than repeat the
-      // global activation, whose loads and epoch CAS would all hit one slot.
-      // Bounded: after the limit the thread activates the block itself.
-      int pool = *((volatile int*)(t.cpool + q));
-      for (int it = 0; pool == kCachePending && it < kCacheWait; ++it) {
-        __nanosleep(32);
-        pool = *((volatile int*)(t.cpool + q));
-      }
+      const int pool = *((volatile int*)(t.cpool + q));
       return pool != kCachePending ? pool : global_activate(m, key, ep);
     }
   }
@@ -320,7 +311,7 @@ __device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& 
   }
   const TilePoints tp(sc, tile);
   const int iters = tile_iters(sc);
-  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u;   // this scan's epoch
+  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u + sc.epoch_add;   // this scan's epoch
   Fixed fx;
   if (kLocal) {
     for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;
@@ -614,7 +605,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
   }
   const TilePoints tp(sc, tile);
   const int iters = tile_iters(sc);
-  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u;   // this scan's epoch
+  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u + sc.epoch_add;   // this scan's epoch
   Fixed fx;
   if (kLocal) {
     for (int q = tid; q < lb; q += kTileThreads) t.mkey[q] = kEmptyKey;

@@ -54,14 +54,16 @@ __device__ __forceinline__ bool pt_valid(const float* P, int sensor) {
 constexpr int kFtW = 32, kFtH = 8, kHalo = 2;
 constexpr int kFsW = kFtW + 2 * kHalo, kFsH = kFtH + 2 * kHalo;
 
-__global__ void __launch_bounds__(kFtW * kFtH) features_kernel(const float* __restrict__ pts, int H, int W,
-                                                                 int sensor, float max_range,
-                                                                 float* __restrict__ out) {
-  __shared__ float sp[kFsH][kFsW][3];
-  __shared__ float sz[kFsH][kFsW];
-  __shared__ unsigned char sv[kFsH][kFsW];
-  const int tiles_x = (W + kFtW - 1) / kFtW;
-  const int x0 = (blockIdx.x % tiles_x) * kFtW - kHalo, y0 = (blockIdx.x / tiles_x) * kFtH - kHalo;
+// The tile of a CTA and its 2-pixel halo in shared memory: points, validity
+// and depth (z for a pinhole, range for a spherical sensor).
+struct FeatTile {
+  float sp[kFsH][kFsW][3];
+  float sz[kFsH][kFsW];
+  unsigned char sv[kFsH][kFsW];
+};
+
+__device__ __forceinline__ void stage_tile(FeatTile& T, const float* __restrict__ pts, int H, int W, int sensor,
+                                           int x0, int y0) {
   for (int q = threadIdx.x; q < kFsW * kFsH; q += blockDim.x) {
     const int ly = q / kFsW, lx = q % kFsW, gx = x0 + lx, gy = y0 + ly;
     float P0 = NAN, P1 = NAN, P2 = NAN;
@@ -71,61 +73,76 @@ __global__ void __launch_bounds__(kFtW * kFtH) features_kernel(const float* __re
     }
     const float Pv[3] = {P0, P1, P2};
     const bool ok = pt_valid(Pv, sensor);
-    sp[ly][lx][0] = P0; sp[ly][lx][1] = P1; sp[ly][lx][2] = P2;
-    sv[ly][lx] = ok;
-    sz[ly][lx] = ok ? (sensor == 0 ? P2 : sqrtf(P0 * P0 + P1 * P1 + P2 * P2)) : 0.0f;
+    T.sp[ly][lx][0] = P0; T.sp[ly][lx][1] = P1; T.sp[ly][lx][2] = P2;
+    T.sv[ly][lx] = ok;
+    T.sz[ly][lx] = ok ? (sensor == 0 ? P2 : sqrtf(P0 * P0 + P1 * P1 + P2 * P2)) : 0.0f;
   }
-  __syncthreads();
-  const int tx = threadIdx.x % kFtW, ty = threadIdx.x / kFtW;
-  const int u = x0 + kHalo + tx, v = y0 + kHalo + ty;
-  if (u >= W || v >= H) return;
+}
+
+// Features of the point at tile position (tx, ty), image pixel (u, v).
+__device__ __forceinline__ void point_features(const FeatTile& T, int tx, int ty, int u, int v, int H, int W,
+                                               float max_range, float f[3]) {
   const int cx = tx + kHalo, cy = ty + kHalo;
-  float f[3] = {0.f, 0.f, 0.f};
-  if (sv[cy][cx]) {
-    const float* P = sp[cy][cx];
-    const float r = sqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
-    f[0] = r / max_range;
-    float th = 0.0f;
-    if (u > 0 && u < W - 1 && v > 0 && v < H - 1 && sv[cy][cx - 1] && sv[cy][cx + 1] && sv[cy - 1][cx] &&
-        sv[cy + 1][cx]) {
-      const float* L = sp[cy][cx - 1];
-      const float* R = sp[cy][cx + 1];
-      const float* U = sp[cy - 1][cx];
-      const float* Dn = sp[cy + 1][cx];
-      const float a0 = R[0] - L[0], a1 = R[1] - L[1], a2 = R[2] - L[2];
-      const float b0 = Dn[0] - U[0], b1 = Dn[1] - U[1], b2 = Dn[2] - U[2];
-      const float n0 = a1 * b2 - a2 * b1, n1 = a2 * b0 - a0 * b2, n2 = a0 * b1 - a1 * b0;
-      const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
-      if (nn > 0.0f) th = acosf(fminf(fabsf(n0 * P[0] + n1 * P[1] + n2 * P[2]) / (nn * r), 1.0f));
-    }
-    f[1] = th / 1.57079632679489662f;
-    // 5x5 window (clipped at the image border: out-of-image points are invalid)
-    float sum = 0.0f;
-    int cnt = 0;
+  f[0] = f[1] = f[2] = 0.0f;
+  if (!T.sv[cy][cx]) return;
+  const float* P = T.sp[cy][cx];
+  const float r = sqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+  f[0] = r / max_range;
+  float th = 0.0f;
+  if (u > 0 && u < W - 1 && v > 0 && v < H - 1 && T.sv[cy][cx - 1] && T.sv[cy][cx + 1] && T.sv[cy - 1][cx] &&
+      T.sv[cy + 1][cx]) {
+    const float* L = T.sp[cy][cx - 1];
+    const float* R = T.sp[cy][cx + 1];
+    const float* U = T.sp[cy - 1][cx];
+    const float* Dn = T.sp[cy + 1][cx];
+    const float a0 = R[0] - L[0], a1 = R[1] - L[1], a2 = R[2] - L[2];
+    const float b0 = Dn[0] - U[0], b1 = Dn[1] - U[1], b2 = Dn[2] - U[2];
+    const float n0 = a1 * b2 - a2 * b1, n1 = a2 * b0 - a0 * b2, n2 = a0 * b1 - a1 * b0;
+    const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+    if (nn > 0.0f) th = acosf(fminf(fabsf(n0 * P[0] + n1 * P[1] + n2 * P[2]) / (nn * r), 1.0f));
+  }
+  f[1] = th / 1.57079632679489662f;
+  // 5x5 window (clipped at the image border: out-of-image points are invalid)
+  float sum = 0.0f;
+  int cnt = 0;
+#pragma unroll
+  for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+    for (int dx = -2; dx <= 2; ++dx)
+      if (T.sv[cy + dy][cx + dx]) {
+        sum += T.sz[cy + dy][cx + dx];
+        ++cnt;
+      }
+  float var = 0.0f;
+  if (cnt >= 3) {
+    const float mu = sum / cnt;
+    float ss = 0.0f;
 #pragma unroll
     for (int dy = -2; dy <= 2; ++dy)
 #pragma unroll
       for (int dx = -2; dx <= 2; ++dx)
-        if (sv[cy + dy][cx + dx]) {
-          sum += sz[cy + dy][cx + dx];
-          ++cnt;
+        if (T.sv[cy + dy][cx + dx]) {
+          const float e = T.sz[cy + dy][cx + dx] - mu;
+          ss += e * e;
         }
-    float var = 0.0f;
-    if (cnt >= 3) {
-      const float mu = sum / cnt;
-      float ss = 0.0f;
-#pragma unroll
-      for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-        for (int dx = -2; dx <= 2; ++dx)
-          if (sv[cy + dy][cx + dx]) {
-            const float e = sz[cy + dy][cx + dx] - mu;
-            ss += e * e;
-          }
-      var = ss / cnt;
-    }
-    f[2] = logf(var + 1e-8f) / 10.0f;
+    var = ss / cnt;
   }
+  f[2] = logf(var + 1e-8f) / 10.0f;
+}
+
+__global__ void __launch_bounds__(kFtW * kFtH) features_kernel(const float* __restrict__ pts, int H, int W,
+                                                                 int sensor, float max_range,
+                                                                 float* __restrict__ out) {
+  __shared__ FeatTile T;
+  const int tiles_x = (W + kFtW - 1) / kFtW;
+  const int x0 = (blockIdx.x % tiles_x) * kFtW - kHalo, y0 = (blockIdx.x / tiles_x) * kFtH - kHalo;
+  stage_tile(T, pts, H, W, sensor, x0, y0);
+  __syncthreads();
+  const int tx = threadIdx.x % kFtW, ty = threadIdx.x / kFtW;
+  const int u = x0 + kHalo + tx, v = y0 + kHalo + ty;
+  if (u >= W || v >= H) return;
+  float f[3];
+  point_features(T, tx, ty, u, v, H, W, max_range, f);
   const size_t idx = (size_t)v * W + u;
   out[3 * idx] = f[0];
   out[3 * idx + 1] = f[1];
@@ -505,6 +522,160 @@ __global__ void __launch_bounds__(32 * kIWarps) mlp_infer_kernel(const float* __
   }
 }
 
+// ------------------------------------------------ fused features + network
+// Per-point weights of an organised scan in one pass: each CTA stages a
+// 32 x 8 pixel tile (and halo) in shared memory, every thread computes its
+// point's features, and each warp (one row of 32 pixels, two 16-point row
+// blocks) runs the network on the tensor cores with mma.sync m16n8k16 BF16
+// fragments that stay in registers from layer to layer: the FP32 accumulator
+// layout of a 16 x 8 output tile, two tiles side by side, is the A-operand
+// layout of the next layer's 16-wide K slice, so ReLU, bias and the BF16
+// rounding are applied in place.  The output layer (32 -> 1) is a dot product
+// of each lane's eight BF16 activations per row with W3, summed over the four
+// lanes of a row.  Same roundings as mlp_infer_kernel: BF16 operands of both
+// GEMMs, FP32 accumulation, W3 and the biases in FP32.
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+struct WeightParamsSmem {
+  float w1[kH * kIn], b1[kH], w2[kH * kH], b2[kH], w3[kH], b3;
+};
+
+__global__ void __launch_bounds__(kFtW * kFtH) point_weights_kernel(const float* __restrict__ params,
+                                                                      const float* __restrict__ pts, int H, int W,
+                                                                      int sensor, float max_range,
+                                                                      float* __restrict__ wout) {
+  __shared__ FeatTile T;
+  __shared__ WeightParamsSmem S;
+  for (int q = threadIdx.x; q < kP; q += blockDim.x) {
+    const float p = params[q];
+    if (q < kOB1) S.w1[q] = p;
+    else if (q < kOW2) S.b1[q - kOB1] = p;
+    else if (q < kOB2) S.w2[q - kOW2] = p;
+    else if (q < kOW3) S.b2[q - kOB2] = p;
+    else if (q < kOB3) S.w3[q - kOW3] = p;
+    else S.b3 = p;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+  // B fragments (col-major K x N, B[k][n] = W[n][k]) of both layers, and the
+  // per-column biases / output weights this lane's accumulator columns see
+  uint32_t B1[4], B2[4][2][2];
+  float b1c[4][2], b2c[4][2], w3c[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int n = nt * 8 + g;
+    const int k0 = tig * 2;
+    B1[nt] = pack_bf16(k0 < kIn ? S.w1[n * kIn + k0] : 0.0f, k0 + 1 < kIn ? S.w1[n * kIn + k0 + 1] : 0.0f);
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      const int k = kt * 16 + tig * 2;
+      B2[nt][kt][0] = pack_bf16(S.w2[n * kH + k], S.w2[n * kH + k + 1]);
+      B2[nt][kt][1] = pack_bf16(S.w2[n * kH + k + 8], S.w2[n * kH + k + 9]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int col = nt * 8 + tig * 2 + j;
+      b1c[nt][j] = S.b1[col];
+      b2c[nt][j] = S.b2[col];
+      w3c[nt][j] = S.w3[col];
+    }
+  }
+  const float b3 = S.b3;
+  const int tiles_x = (W + kFtW - 1) / kFtW;
+  const int n_tiles = tiles_x * ((H + kFtH - 1) / kFtH);
+  const int tx = threadIdx.x % kFtW, ty = threadIdx.x / kFtW;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int x0 = (tile % tiles_x) * kFtW - kHalo, y0 = (tile / tiles_x) * kFtH - kHalo;
+    __syncthreads();   // the previous tile's staging is no longer read
+    stage_tile(T, pts, H, W, sensor, x0, y0);
+    __syncthreads();
+    const int u = x0 + kHalo + tx, v = y0 + kHalo + ty;
+    float f[3] = {0.0f, 0.0f, 0.0f};
+    if (u < W && v < H) point_features(T, tx, ty, u, v, H, W, max_range, f);
+    float wpt[2] = {0.0f, 0.0f};   // this lane's output rows g and g + 8 of each row block
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      // layer 1: A = features of points mt*16 + g and + 8 (K padded to 16)
+      const int pa = mt * 16 + g, pb = pa + 8;
+      const float fa0 = __shfl_sync(0xffffffffu, f[0], pa), fa1 = __shfl_sync(0xffffffffu, f[1], pa);
+      const float fa2 = __shfl_sync(0xffffffffu, f[2], pa);
+      const float fb0 = __shfl_sync(0xffffffffu, f[0], pb), fb1 = __shfl_sync(0xffffffffu, f[1], pb);
+      const float fb2 = __shfl_sync(0xffffffffu, f[2], pb);
+      uint32_t A[4];
+      A[0] = tig == 0 ? pack_bf16(fa0, fa1) : (tig == 1 ? pack_bf16(fa2, 0.0f) : 0u);
+      A[1] = tig == 0 ? pack_bf16(fb0, fb1) : (tig == 1 ? pack_bf16(fb2, 0.0f) : 0u);
+      A[2] = 0u;
+      A[3] = 0u;
+      float C[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        C[nt][0] = C[nt][1] = C[nt][2] = C[nt][3] = 0.0f;
+        mma_bf16_16816(C[nt], A, B1[nt], 0u);
+      }
+      // h1 = relu(. + b1), rounded to BF16: the A operand of layer 2
+      uint32_t A2[2][4];
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int nt = 2 * kt + h;
+          A2[kt][2 * h] = pack_bf16(fmaxf(C[nt][0] + b1c[nt][0], 0.0f), fmaxf(C[nt][1] + b1c[nt][1], 0.0f));
+          A2[kt][2 * h + 1] = pack_bf16(fmaxf(C[nt][2] + b1c[nt][0], 0.0f), fmaxf(C[nt][3] + b1c[nt][1], 0.0f));
+        }
+      }
+      // the A layout wants {row g, cols k..k+1}, {row g+8, k..}, {row g, k+8..}, {row g+8, k+8..}
+      uint32_t A2r[2][4];
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) {
+        A2r[kt][0] = A2[kt][0];
+        A2r[kt][1] = A2[kt][1];
+        A2r[kt][2] = A2[kt][2];
+        A2r[kt][3] = A2[kt][3];
+      }
+      // layer 2
+      float D[4][4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        D[nt][0] = D[nt][1] = D[nt][2] = D[nt][3] = 0.0f;
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt) mma_bf16_16816(D[nt], A2r[kt], B2[nt][kt][0], B2[nt][kt][1]);
+      }
+      // output layer on BF16(relu(. + b2))
+      float oa = 0.0f, ob = 0.0f;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          oa += w3c[nt][j] * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][j] + b2c[nt][j], 0.0f)));
+          ob += w3c[nt][j] * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][2 + j] + b2c[nt][j], 0.0f)));
+        }
+      oa += __shfl_xor_sync(0xffffffffu, oa, 1);
+      oa += __shfl_xor_sync(0xffffffffu, oa, 2);
+      ob += __shfl_xor_sync(0xffffffffu, ob, 1);
+      ob += __shfl_xor_sync(0xffffffffu, ob, 2);
+      wpt[mt] = tig == 0 ? softplus_f(oa + b3) : (tig == 1 ? softplus_f(ob + b3) : 0.0f);
+    }
+    // lane (g, tig) holds the weights of points mt*16 + g (tig 0) and + 8 (tig 1)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int pt = mt * 16 + g + (tig == 1 ? 8 : 0);
+      const int gu = x0 + kHalo + pt;
+      if (tig < 2 && gu < W && v < H) wout[(size_t)v * W + gu] = wpt[mt];
+    }
+  }
+}
+
 // Target normalisation: per-CTA partial sums of e2 * mask and mask over a
 // fixed grid-stride partition, summed in CTA order by one thread (so the mean
 // does not depend on scheduling), then every target divided by the mean.
@@ -664,6 +835,19 @@ cvx_status cvx_weight_model_infer(cvx_weight_model* w, const float* features, in
   const long long tiles = (n + 15) / 16;
   const int grid = (int)std::min<long long>((tiles + kIWarps - 1) / kIWarps, (long long)num_sms() * 4);
   COVOX_LAUNCH(kKMlpFwd, s, mlp_infer_kernel<<<grid, 32 * kIWarps, 0, s>>>(w->params, features, n, weights));
+  return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
+}
+
+cvx_status cvx_weight_model_point_weights(cvx_weight_model* w, const float* points, int32_t height, int32_t width,
+                                          int32_t sensor, float max_range, float* weights, void* stream) {
+  if (!w || !points || !weights || height <= 0 || width <= 0 || (sensor != 0 && sensor != 1) || !(max_range > 0))
+    return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int tiles = ((width + kFtW - 1) / kFtW) * ((height + kFtH - 1) / kFtH);
+  const int grid = std::min(tiles, num_sms() * 4);
+  COVOX_LAUNCH(kKMlpFwd, s,
+               point_weights_kernel<<<grid, kFtW * kFtH, 0, s>>>(w->params, points, height, width, sensor,
+                                                                  max_range, weights));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
 

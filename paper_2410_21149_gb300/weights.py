@@ -134,9 +134,13 @@ def train(model: WeightModel, feats, e2, mask, steps: int = 400, batch: int = 65
 
 
 def learned_point_weights(model: WeightModel, scan_points, height: int, width: int, sensor: int,
-                          max_range: float):
-    """Per-point weights of one organised scan (device [N])."""
-    return model.infer(features(scan_points, height, width, sensor, max_range))
+                          max_range: float, out=None, stream=None):
+    """Per-point weights of one organised scan (device [N]): features and
+    network in one fused kernel."""
+    import torch
+    w = torch.empty(height * width, dtype=torch.float32, device=scan_points.device) if out is None else out
+    _capi.cvx_weight_model_point_weights(model.handle, scan_points, height, width, sensor, max_range, w, stream)
+    return w
 
 
 def gate(rmse_learned: float, rmse_plain: float) -> bool:

@@ -112,3 +112,39 @@ def test_registration_points_and_bounds_by_hand():
     want = np.array([[-0.05, 1.65, 0.15], [0.05, 0.05, 0.05]], np.float32)
     assert np.allclose(pts, want, rtol=0, atol=1e-7)
     assert np.allclose(oe.submap_bounds(keys, 0.1), [-0.8, 0.0, 0.0, 0.8, 2.4, 0.8], atol=1e-6)
+
+
+# ------------------------------------------------------------- submap overlap
+def _T(R=np.eye(3), t=(0, 0, 0)):
+    return np.concatenate([np.asarray(R, np.float64), np.asarray(t, np.float64)[:, None]], 1).reshape(12)
+
+
+def test_overlap_identity_poses_closed_form():
+    from oracle import esdf as oe
+    a = [0, 0, 0, 2, 3, 4]
+    b = [1, 1, 1, 5, 2, 2]
+    v, box = oe.submap_overlap(a, _T(), b, _T())
+    assert v == 1 * 1 * 1 and list(box) == [1, 1, 1, 2, 2, 2]
+    v, _ = oe.submap_overlap(a, _T(), a, _T())
+    assert v == 24.0                                     # a box with itself
+    v, _ = oe.submap_overlap(a, _T(), b, _T(t=(10, 0, 0)))
+    assert v == 0.0                                      # disjoint
+    v, _ = oe.submap_overlap([0, 0, 0, 4, 4, 4], _T(), [1, 1, 1, 2, 2, 2], _T())
+    assert v == 1.0                                      # containment: the smaller box
+    v, _ = oe.submap_overlap([1, 1, 1, 0, 0, 0], _T(), a, _T())
+    assert v == 0.0                                      # empty submap
+
+
+def test_overlap_quarter_turn_and_translation():
+    """A quarter turn about z maps the box x in [0,2], y in [0,1] to x in
+    [-1,0], y in [0,2]; shifted by (+1, 0, 0) it overlaps [0,1]^2 x [0,1] in
+    [0,1] x [0,1] x [0,1]."""
+    from oracle import esdf as oe
+    Rz = [[0, -1, 0], [1, 0, 0], [0, 0, 1]]
+    v, box = oe.submap_overlap([0, 0, 0, 2, 1, 1], _T(Rz, (1, 0, 0)), [0, 0, 0, 1, 1, 1], _T())
+    assert abs(v - 1.0) < 1e-15 and np.allclose(box, [0, 0, 0, 1, 1, 1])
+    # a 45 degree turn: the world box of the unit square spans sqrt(2)
+    c = np.sqrt(0.5)
+    v, box = oe.submap_overlap([0, 0, 0, 1, 1, 1], _T([[c, -c, 0], [c, c, 0], [0, 0, 1]]), [-5, -5, -5, 5, 5, 5],
+                               _T())
+    assert abs((box[3] - box[0]) - np.sqrt(2)) < 1e-12 and abs(v - 2.0) < 1e-12

@@ -118,3 +118,44 @@ def test_registration_points_and_bounds(storage):
     assert _capi.cvx_registration_points(sub.handle, w_min, band, small) == n   # count beyond capacity
     assert np.array_equal(_capi.cvx_submap_bounds(sub.handle), oe.submap_bounds(keys, np.float32(sub.voxel_size)))
     sub.close()
+
+
+def test_submap_overlaps_match_oracle():
+    """cvx_submap_overlaps on the bounds of real LiDAR submaps with their
+    poses, plus rotated and empty ones, against the FP64 oracle (volumes
+    within FP32 rounding of the transformed corners)."""
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    from oracle import esdf as oe
+    wl = sg.make_c3(n_scans=8, scans_per_submap=2, n_boxes=300)
+    bounds, poses = [], []
+    for sm in wl.submaps:
+        sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, 0, max_blocks=1 << 14)
+        for sc in sm.scans:
+            sub.integrate(torch.from_numpy(sc.points).cuda(), sc.T_sub_sensor,
+                          cvx.integrate_params(0, 0, wl.min_range, wl.max_range, 1, 64, 1024))
+        bounds.append(cvx._capi.cvx_submap_bounds(sub.handle))
+        poses.append(np.asarray(sm.T_world_sub, np.float32).reshape(12))
+        sub.close()
+    rng = np.random.default_rng(2)
+    ang = rng.uniform(0, 2 * np.pi)
+    R = np.array([[np.cos(ang), -np.sin(ang), 0], [np.sin(ang), np.cos(ang), 0], [0, 0, 1]])
+    bounds.append(bounds[0])
+    poses.append(np.concatenate([R, np.asarray(poses[0]).reshape(3, 4)[:, 3:]], 1).reshape(12).astype(np.float32))
+    bounds.append(np.array([1, 1, 1, 0, 0, 0], np.float32))          # empty submap
+    poses.append(np.eye(3, 4, dtype=np.float32).reshape(12))
+    B = torch.from_numpy(np.stack(bounds).astype(np.float32)).cuda()
+    P = torch.from_numpy(np.stack(poses).astype(np.float32)).cuda()
+    vol, boxes = cvx._capi.cvx_submap_overlaps(B, P, with_boxes=True)
+    vol, boxes = vol.cpu().numpy(), boxes.cpu().numpy()
+    n = len(bounds)
+    nonzero = 0
+    for i in range(n):
+        for j in range(n):
+            v, box = oe.submap_overlap(bounds[i], poses[i], bounds[j], poses[j])
+            assert abs(vol[i, j] - v) <= 1e-5 * max(v, 1.0) + 1e-4, (i, j, vol[i, j], v)
+            if v > 0:
+                assert np.abs(boxes[i, j] - box).max() < 1e-4
+                nonzero += 1
+    assert nonzero >= n                        # at least every submap with itself
+    assert vol[n - 1].max() == 0 and vol[:, n - 1].max() == 0

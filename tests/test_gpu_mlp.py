@@ -222,3 +222,29 @@ def test_normalise_targets_on_device():
     assert np.allclose(out.cpu().numpy(), e2 / np.float32(mean), rtol=2e-7, atol=0)
     out2, mean2 = weights.normalise_targets(torch.from_numpy(e2).cuda(), torch.from_numpy(mask).cuda())
     assert mean2 == mean and torch.equal(out, out2)
+
+
+def test_fused_point_weights_match_features_then_inference():
+    """cvx_weight_model_point_weights (features and network in one kernel,
+    layer-to-layer activations in mma.sync fragments) against the two-kernel
+    path (cvx_point_features, then cvx_weight_model_infer) and the FP64
+    oracle, on a 640x480 frame (ragged tile rows) and a 64x1024 scan."""
+    import torch
+    from paper_2410_21149_gb300 import _capi, weights
+    p = _rand_params(3)
+    m = weights.WeightModel(omlp.flatten(p).astype(np.float32))
+    q = omlp.unflatten(omlp.flatten(p).astype(np.float32).astype(np.float64))
+    cases = [(_scan(seed=22, W=640, H=478).submaps[0].scans[1], 0, 10.0),
+             (sg.make_c3(n_scans=2, scans_per_submap=2, n_boxes=300).submaps[0].scans[1], 1, 50.0)]
+    for sc, sensor, max_range in cases:
+        pts = torch.from_numpy(sc.points).cuda()
+        fused = weights.learned_point_weights(m, pts, sc.height, sc.width, sensor, max_range).cpu().numpy()
+        two = m.infer(weights.features(pts, sc.height, sc.width, sensor, max_range)).cpu().numpy()
+        rel = np.abs(fused / two - 1)
+        assert np.isfinite(fused).all() and rel.max() < 4e-3 and np.mean(rel > 1e-4) < 0.01, rel.max()
+        f_orc = omlp.features(sc.points, sc.height, sc.width, sensor, max_range)
+        w_orc, _ = omlp.forward(q, f_orc)
+        valid = np.isfinite(sc.points).all(1)
+        rel_o = np.abs(fused / w_orc - 1)[valid]
+        assert np.quantile(rel_o, 0.999) < 1e-2, np.quantile(rel_o, 0.999)
+    m.close()
