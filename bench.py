@@ -208,7 +208,7 @@ def multi_rmse(wl, subs, storage):
 
 
 def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=True, tune_force=False,
-                pipelined=True):
+                pipelined=True, sets=4):
     """Many submaps: one batched persistent launch per step (autotuned tile
     shape, CUDA graph), beside the same scans through the per-scan path."""
     import torch
@@ -216,7 +216,7 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
     from paper_2410_21149_gb300 import _capi, autotune
     stream = torch.cuda.Stream()
     subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
-                       pipelined=pipelined) for sm in wl.submaps]
+                       pipelined=pipelined, sets=sets) for sm in wl.submaps]
     handles = [s.handle for s in subs]
     # every scan's points in one device buffer (views per scan) with a pinned
     # host copy for the end-to-end timing
@@ -241,7 +241,7 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
             s.reset(st)
 
     tuned = autotune.tune_batch(handles, [(m, p, T, None, prm(sc)) for m, p, T, sc in items],
-                                f"{wl.name}|st{storage}|p{int(pipelined)}", reset=reset, force=tune_force)
+                                f"{wl.name}|st{storage}|p{int(pipelined)}|s{sets}", reset=reset, force=tune_force)
     ppc, lb = tuned["pts_per_cta"], tuned["local_blocks"]
     bscans = [(m, p, T, None, prm(sc, ppc, lb)) for m, p, T, sc in items]
     batch = _capi.cvx_batch_create(len(subs), len(bscans))
@@ -335,7 +335,7 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
 def run_ours(args):
     import torch
     import paper_2410_21149_gb300 as cvx
-    from paper_2410_21149_gb300 import _capi
+    from paper_2410_21149_gb300 import _capi, autotune
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev_index = torch.cuda.current_device()
@@ -351,45 +351,25 @@ def run_ours(args):
     pts = host.cuda()
     Ts = [s.T_sub_sensor for s in sm.scans]
     sc0 = sm.scans[0]
+    stream = torch.cuda.Stream()
+    max_blocks = args.max_blocks
 
     def prm_of(ppc, lb):
         return cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range, sc0.sensor,
                                     sc0.height, sc0.width, ppc, lb)
 
-    pipelined = args.pipelined == 1
-    tune_report = None
-    if args.ppc == 0:   # launch shape from the autotuner (first 20 frames, cached per device)
-        from paper_2410_21149_gb300 import autotune
-        sample = [(pts[f], Ts[f]) for f in range(min(20, len(Ts)))]
-        tuned = {p: autotune.tune_scans(sm.voxel_size, sm.trunc, wl.max_weight, 0, sample, prm_of,
-                                        max_blocks=args.max_blocks, pipelined=p)
-                 for p in ((False, True) if args.pipelined < 0 else (pipelined,))}
-        pipelined = min(tuned, key=lambda p: tuned[p]["ms"])
-        args.ppc, args.lb = tuned[pipelined]["pts_per_cta"], tuned[pipelined]["local_blocks"]
-        tune_report = {("pipelined" if p else "plain"): tuned[p]["timings"] for p in tuned}
-    params = prm_of(args.ppc, args.lb)
-    stream = torch.cuda.Stream()
-    max_blocks = args.max_blocks
-
-    def make_sub(storage):
+    def make_sub(storage, sets=4, pipelined=True):
         with torch.cuda.stream(stream):
-            s = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
-                           stream=stream, pipelined=pipelined)
-        return s
+            return cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, storage, max_blocks=max_blocks,
+                              stream=stream, pipelined=pipelined, sets=sets)
 
-    def step(sub):
-        sub.reset(stream)
-        for f in range(F):
-            sub.integrate(pts[f], Ts[f], params, None, stream)
-        sub.flush(stream)     # pipelined submap: the last frame's merge (no-op otherwise)
-
-    def capture(sub):
+    def capture(step):
         for _ in range(2):      # warm up the allocator and the kernels outside capture
-            step(sub)
+            step()
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            step(sub)
+            step()
         torch.cuda.synchronize()
         return g
 
@@ -407,68 +387,113 @@ def run_ours(args):
             barrier(ws)
         return e0.elapsed_time(e1)
 
+    def profiled(step, steps):
+        """Library kernels of `steps` eager steps, each launch bracketed by CUDA
+        events on its stream; and the launches one step issues."""
+        _capi.cvx_profile_start(1 << 22)
+        l0 = _capi.cvx_launch_count()
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        n = (_capi.cvx_launch_count() - l0) // steps
+        _capi.cvx_profile_stop()
+        return _capi.cvx_profile_read(), n
+
+    # ---- the headline path: all frames of the step in one batched persistent
+    # launch, four per-scan sets (several frames in flight), shape autotuned
+    sample = list(range(min(40, F)))
+    if args.ppc == 0:
+        tsub = make_sub(cvx.CVX_STORE_F32)
+        tuned = autotune.tune_batch([tsub.handle], [(0, pts[f], Ts[f], None, prm_of(0, 0)) for f in sample],
+                                    f"{wl.name}|st0|s4|{len(sample)}", reset=lambda: tsub.reset())
+        tsub.close()
+        args.ppc, args.lb = tuned["pts_per_cta"], tuned["local_blocks"]
+        tune_report = tuned["timings"]
+    else:
+        tune_report = None
+    params = prm_of(args.ppc, args.lb)
+    scans_all = [(0, pts[f], Ts[f], None, params) for f in range(F)]
+
+    def batched_step(sub, batch, scans):
+        sub.reset(stream)
+        _capi.cvx_integrate_batch(batch, [sub.handle], scans, stream)
+
     sub32 = make_sub(cvx.CVX_STORE_F32)
-    g32 = capture(sub32)
-    # counters of exactly one step (reset clears them)
-    step(sub32)
+    batch32 = _capi.cvx_batch_create(1, F)
+    step32 = lambda: batched_step(sub32, batch32, scans_all)   # noqa: E731
+    g32 = capture(step32)
+    step32()
     torch.cuda.synchronize()
     c1 = sub32.counters()
+    assert _capi.cvx_batch_error(batch32) == 0 and sub32.status() == 0, "device error in the benchmark workload"
     keys, D, W = (t.cpu().numpy() for t in sub32.extract(stream))
     rmse32 = sdf_rmse(wl.scene, keys, D.astype(np.float64), W.astype(np.float64), sm.voxel_size, sm.trunc)
-    assert sub32.status() == 0, "device error during the benchmark workload"
 
     clocks = Clocks(dev_index)
     clocks.start()
     ms32 = timed(g32, args.steps, args.warmup)
     clk = clocks.stop()
     ms32 = max_over_ranks(ms32, ws)
+    prof, launches_per_step = profiled(step32, args.steps)
 
-    # per-kernel durations: profiled eager pass over the same steps (the
-    # library counts every launch it issues: one step's count checks the
-    # launches the captured graph replays)
-    _capi.cvx_profile_start(1 << 22)
-    l0 = _capi.cvx_launch_count()
-    for _ in range(args.steps):
-        step(sub32)
-    torch.cuda.synchronize()
-    launches_per_step = (_capi.cvx_launch_count() - l0) // args.steps
-    _capi.cvx_profile_stop()
-    prof = _capi.cvx_profile_read()
-
-    # FP16 storage form
+    # FP16 storage form, same path
     sub16 = make_sub(cvx.CVX_STORE_F16)
-    g16 = capture(sub16)
-    step(sub16)
+    batch16 = _capi.cvx_batch_create(1, F)
+    step16 = lambda: batched_step(sub16, batch16, scans_all)   # noqa: E731
+    g16 = capture(step16)
+    step16()
     torch.cuda.synchronize()
     keys16, D16, W16 = (t.cpu().numpy() for t in sub16.extract(stream))
     D16 = D16.astype(np.float64) * np.float64(np.float32(sm.trunc))
     rmse16 = sdf_rmse(wl.scene, keys16, D16, W16.astype(np.float64), sm.voxel_size, sm.trunc)
-    ms16 = timed(g16, args.steps, args.warmup)
-    ms16 = max_over_ranks(ms16, ws)
-    _capi.cvx_profile_start(1 << 22)
-    for _ in range(args.steps):
-        step(sub16)
-    torch.cuda.synchronize()
-    _capi.cvx_profile_stop()
-    prof16 = _capi.cvx_profile_read()
+    ms16 = max_over_ranks(timed(g16, args.steps, args.warmup), ws)
+    prof16, _ = profiled(step16, args.steps)
 
-    # end to end: pinned host points copied in on a side stream (double
-    # buffered), integrated through the public API, counters read back
+    # the per-scan path on the same frames (two launches per frame, shape and
+    # schedule autotuned), for comparison
+    ps_sample = [(pts[f], Ts[f]) for f in range(min(20, F))]
+    ps_tuned = {p: autotune.tune_scans(sm.voxel_size, sm.trunc, wl.max_weight, 0, ps_sample, prm_of,
+                                       max_blocks=max_blocks, pipelined=p) for p in (False, True)}
+    ps_pipe = min(ps_tuned, key=lambda p: ps_tuned[p]["ms"])
+    ps_params = prm_of(ps_tuned[ps_pipe]["pts_per_cta"], ps_tuned[ps_pipe]["local_blocks"])
+    sub_ps = make_sub(cvx.CVX_STORE_F32, sets=2 if ps_pipe else 1, pipelined=ps_pipe)
+
+    def step_ps():
+        sub_ps.reset(stream)
+        for f in range(F):
+            sub_ps.integrate(pts[f], Ts[f], ps_params, None, stream)
+        sub_ps.flush(stream)
+
+    ms_ps = max_over_ranks(timed(capture(step_ps), max(3, args.steps // 2), args.warmup), ws) / max(3, args.steps // 2)
+    prof_ps, _ = profiled(step_ps, 2)
+    sub_ps.close()
+
+    # end to end through the public API: each step copies its frames from
+    # pinned host memory in four chunks on a side stream (double buffered),
+    # one batched launch per chunk as its copy lands, counters read back
     copy_stream = torch.cuda.Stream()
-    bufs = [torch.empty((N, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    n_chunks = 4
+    chunk = (F + n_chunks - 1) // n_chunks
+    bufs = [torch.empty((chunk, N, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
     ev_copied = [torch.cuda.Event() for _ in range(2)]
     ev_used = [torch.cuda.Event() for _ in range(2)]
+    chunk_batches, chunk_scans = [], []
+    for c in range(n_chunks):
+        f0, f1 = c * chunk, min(F, (c + 1) * chunk)
+        chunk_batches.append(_capi.cvx_batch_create(1, chunk))
+        chunk_scans.append([(0, bufs[c % 2][f - f0], Ts[f], None, params) for f in range(f0, f1)])
 
     def e2e_step():
         sub32.reset(stream)
-        for f in range(F):
-            b = f & 1
+        for c in range(n_chunks):
+            b = c % 2
+            f0, f1 = c * chunk, min(F, (c + 1) * chunk)
             copy_stream.wait_event(ev_used[b])
             with torch.cuda.stream(copy_stream):
-                bufs[b].copy_(host[f], non_blocking=True)
+                bufs[b][: f1 - f0].copy_(host[f0:f1], non_blocking=True)
                 ev_copied[b].record(copy_stream)
             stream.wait_event(ev_copied[b])
-            sub32.integrate(bufs[b], Ts[f], params, None, stream)
+            _capi.cvx_integrate_batch(chunk_batches[c], [sub32.handle], chunk_scans[c], stream)
             ev_used[b].record(stream)
         return sub32.counters()   # device -> host read of the step's result
 
@@ -479,9 +504,10 @@ def run_ours(args):
     barrier(ws)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_step()
+        ce = e2e_step()
     barrier(ws)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, ws)
+    assert ce["frames"] == F and ce["valid_points"] == c1["valid_points"]
 
     valid = c1["valid_points"]
     obs = c1["observations"]
@@ -497,9 +523,9 @@ def run_ours(args):
     # roofline of the dominant kernel (algorithmic bytes per launch / event time)
     S32 = 8
     bytes_kernel = {
-        "integrate_kernel": (12 * F * N + 16 * blocks + 12 * new_blocks) / F,
-        "merge_kernel": 2 * S32 * merged / F,
-        "integrate_pipelined_kernel": (12 * F * N + 16 * blocks + 12 * new_blocks + 2 * S32 * merged) / F,
+        # the whole frame sequence: points, hash probes and new keys, D/W of the merged voxels
+        "batched_kernel": 12 * F * N + 16 * blocks + 12 * new_blocks + 2 * S32 * merged,
+        "zero_pool_kernel": S32 * 512 * new_blocks,
     }
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]
@@ -524,12 +550,12 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "frames_per_step": F, "points_per_frame": N,
                    "voxel_size_m": sm.voxel_size, "trunc_m": sm.trunc, "weight": "quadratic+linear-dropoff",
-                   "storage": "f32", "step": "clear submap + integrate all frames (CUDA graph replay)",
-                   "launch_shape": "%d points per CTA, %s, %s submap" % (
-                       args.ppc, "L2 vector reductions" if args.lb < 0 else f"{args.lb or 8} shared block slots",
-                       "pipelined" if pipelined else "plain"),
-                   "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb, "pipelined": pipelined,
-                                 "candidates_ms_20_frames": tune_report},
+                   "storage": "f32",
+                   "step": "clear submap + integrate all frames in one batched persistent launch (CUDA graph replay)",
+                   "launch_shape": "%d points per tile, %s, 4 per-scan sets" % (
+                       args.ppc, "L2 vector reductions" if args.lb < 0 else f"{args.lb or 8} shared block slots"),
+                   "autotuned": {"pts_per_cta": args.ppc, "local_blocks": args.lb,
+                                 "candidates_ms_%d_frames" % len(sample): tune_report},
                    "l2": "inputs (%.0f MB of points) exceed the 129 MB L2" % (F * N * 12 / 1e6),
                    "parallelism": f"replica x{ws} (one submap sequence per GPU)"},
         "voxel_updates_per_s": tot_obs / sec32,
@@ -539,7 +565,13 @@ def run_ours(args):
                             "blocks_touched": blocks, "blocks_allocated": new_blocks},
         "forms": {"fp16_storage": {"points_per_s": tot_valid / sec16, "ms_per_step": ms16 / args.steps,
                                    "speedup_vs_fp32": sec32 / sec16, "sdf_rmse_m": rmse16,
-                                   "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof16.items() if v[1]}}},
+                                   "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof16.items() if v[1]}},
+                  "per_scan_path": {"points_per_s": tot_valid / (ms_ps / 1e3), "ms_per_step": ms_ps,
+                                    "batched_speedup": ms_ps / (ms32 / args.steps),
+                                    "autotuned": {"pts_per_cta": ps_tuned[ps_pipe]["pts_per_cta"],
+                                                  "local_blocks": ps_tuned[ps_pipe]["local_blocks"],
+                                                  "pipelined": ps_pipe},
+                                    "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof_ps.items() if v[1]}}},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": kernel_traffic(dom, args.ppc, args.lb), "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms},
@@ -555,12 +587,15 @@ def run_ours(args):
         "gpu_launches_per_step": launches_per_step,
         "clocks": clk,
     }
+    per_scan_sub = lambda storage: make_sub(storage, sets=2 if ps_pipe else 1, pipelined=ps_pipe)   # noqa: E731
     if not args.no_extra:
-        out["forms"]["carving"] = carving_form(wl, pts, Ts, stream, args, ws, make_sub, capture, timed, prm_of)
+        out["forms"]["carving"] = carving_form(wl, pts, Ts, stream, args, ws, per_scan_sub, None, timed,
+                                               lambda a, b: _capi.cvx_integrate_params.from_buffer_copy(ps_params))
         out["forms"]["esdf"] = esdf_form(sub32, stream, args, peaks)
         out["forms"]["hash_stress"] = hash_stress_form(args)
     if not args.no_learned:
-        out["forms"]["learned_weight"] = learned_form(wl, pts, Ts, stream, args, ws, rmse32, ms32 / args.steps)
+        out["forms"]["learned_weight"] = learned_form(wl, pts, Ts, stream, args, ws, rmse32, ms32 / args.steps,
+                                                      make_sub, capture, timed, params)
     if not args.no_lidar:
         out["forms"]["lidar"] = lidar_form(args, ws, rank, peaks, peak_src)
     if not args.no_batched:
@@ -584,6 +619,8 @@ def run_ours(args):
         out["error_fp32_vs_fp64_oracle"] = err["fp32"]
     if rank == 0:
         print(json.dumps(out), flush=True)
+    for b in [batch32, batch16] + chunk_batches:
+        _capi.cvx_batch_destroy(b)
     for s in (sub32, sub16):
         s.close()
     if ws > 1:
@@ -696,10 +733,10 @@ def hash_stress_form(args, slots_log2=26, load_factors=(0.1, 0.5, 0.85)):
     return res
 
 
-def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):
+def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain, make_sub, capture, timed, params):
     """Learned per-point weight on the multiroom workload: train the network
     on three other seeded buildings (noisy vs noise-free fused TSDF targets),
-    then time features + inference + per-point-weight integration per frame,
+    then time per-frame weights + per-point-weight integration of all frames,
     and compare the SDF RMSE with the plain quadratic weight (gate)."""
     import torch
     import scenegen as sg
@@ -724,44 +761,38 @@ def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     N = sm.scans[0].points.shape[0]
-    wbuf = torch.empty(N, dtype=torch.float32, device="cuda")
-    prm = cvx.integrate_params(cvx.CVX_W_PER_POINT, wl.dropoff, wl.min_range, wl.max_range, 0, H, W, args.ppc,
-                               args.lb)
-    with torch.cuda.stream(stream):
-        sub = cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, 0, max_blocks=args.max_blocks, stream=stream)
+    nf = len(Ts)
+    # every frame's per-point weights (features + network in one fused kernel
+    # per frame), then all frames in one batched persistent launch with
+    # per-point weights: the headline's path and launch shape
+    w_all = torch.empty((nf, N), dtype=torch.float32, device="cuda")
+    prm = _capi.cvx_integrate_params.from_buffer_copy(params)
+    prm.weight_mode = cvx.CVX_W_PER_POINT
+    sub = make_sub(cvx.CVX_STORE_F32)
+    batch = _capi.cvx_batch_create(1, nf)
+    scans_l = [(0, pts[f], Ts[f], w_all[f], prm) for f in range(nf)]
 
     def step():
         sub.reset(stream)
-        for f in range(len(Ts)):
-            # features + network in one fused kernel, then the per-point-weight integration
-            _capi.cvx_weight_model_point_weights(model.handle, pts[f], H, W, 0, wl.max_range, wbuf, stream)
-            sub.integrate(pts[f], Ts[f], prm, wbuf, stream)
+        for f in range(nf):
+            _capi.cvx_weight_model_point_weights(model.handle, pts[f], H, W, 0, wl.max_range, w_all[f], stream)
+        _capi.cvx_integrate_batch(batch, [sub.handle], scans_l, stream)
 
-    for _ in range(2):
-        step()
+    g = capture(step)
+    step()
     torch.cuda.synchronize()
+    assert _capi.cvx_batch_error(batch) == 0 and sub.status() == 0
     keys, D, Wt = (t.cpu().numpy() for t in sub.extract(stream))
     rmse_l = sdf_rmse(wl.scene, keys, D.astype(np.float64), Wt.astype(np.float64), sm.voxel_size, sm.trunc)
     c = sub.counters()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        step()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            g.replay()
-        barrier(ws)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            g.replay()
-        e1.record(stream)
-        barrier(ws)
-    ms = max_over_ranks(e0.elapsed_time(e1), ws) / args.steps
+    ms_total = timed(g, args.steps, args.warmup)
+    ms = max_over_ranks(ms_total, ws) / args.steps
     _capi.cvx_profile_start(1 << 20)
     step()
     torch.cuda.synchronize()
     _capi.cvx_profile_stop()
     prof = _capi.cvx_profile_read()
+    _capi.cvx_batch_destroy(batch)
     sub.close()
     gain = weighting_noise_rmse(model, wl, stream)
     model.close()
@@ -782,7 +813,7 @@ def lidar_numbers(args, ws, peaks, peak_src, storage=0, n_scans=2000):
     import scenegen as sg
     wl = sg.make_c3(n_scans=n_scans)
     hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
-    r = bench_multi(wl, storage, args.steps, args.warmup, ws, max_blocks=1 << 16)
+    r = bench_multi(wl, storage, args.steps, args.warmup, ws, max_blocks=1 << 14)
     pts = sum_over_ranks(r["points"], ws)
     ach = r["kernel_bytes"] / (r["batched_kernel_ms"] / 1e3) / 1e9
     return wl, r, {

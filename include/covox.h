@@ -82,6 +82,12 @@ typedef void (*cvx_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
  * set is in use lives on the device, so recorded CUDA graphs replay
  * correctly. */
 #define CVX_SUBMAP_PIPELINED 1
+/* Four sets of per-scan sums and touch epochs (implies CVX_SUBMAP_PIPELINED):
+ * in a batched launch scan k accumulates into set k mod 4, so its tiles wait
+ * only for the merge of scan k - 4, and several consecutive scans of one
+ * submap are in flight at once (same results; four times the per-scan
+ * memory, 4 KB per block per set).  The per-scan path uses the first two. */
+#define CVX_SUBMAP_FOUR_SETS 2
 
 typedef struct {
   float voxel_size;      /* metres, > 0 */
@@ -90,7 +96,7 @@ typedef struct {
   int32_t storage;       /* cvx_storage */
   int64_t max_blocks;    /* block pool capacity (blocks of 512 voxels) */
   int64_t hash_slots;    /* hash table slots, a power of two >= 2 * max_blocks advised */
-  int64_t flags;         /* 0, or CVX_SUBMAP_PIPELINED */
+  int64_t flags;         /* 0, CVX_SUBMAP_PIPELINED or CVX_SUBMAP_FOUR_SETS */
   cvx_alloc_fn alloc;
   cvx_free_fn free;
   void* alloc_ctx;
@@ -278,8 +284,8 @@ typedef struct cvx_batch cvx_batch;
  * max_scans scans (device memory and pinned host staging).  Synchronous. */
 cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** out);
 
-/* Integrate a batch of scans into distinct submaps with one cooperative
- * persistent kernel (Sec. III-D workload equalisation across scans).  Scans
+/* Integrate a batch of scans into distinct submaps with one persistent
+ * kernel (Sec. III-D workload equalisation across scans).  Scans
  * of one submap are integrated as successive frames in array order (exactly
  * as successive cvx_integrate_scan calls); scans of different submaps are
  * independent; empty scans are skipped.  The kernel takes tile and merge

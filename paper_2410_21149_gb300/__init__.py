@@ -53,7 +53,7 @@ class Submap:
     def __init__(self, voxel_size: float, trunc: float, max_weight: float = 1e4,
                  storage: int = CVX_STORE_F32, max_blocks: int = 1 << 16,
                  hash_slots: Optional[int] = None,
-                 use_torch_allocator: bool = True, stream=None, pipelined: bool = False):
+                 use_torch_allocator: bool = True, stream=None, pipelined: bool = False, sets: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Submap needs a CUDA device; there is no CPU path")
@@ -61,7 +61,9 @@ class Submap:
             hash_slots = 1 << max(1, int(np.ceil(np.log2(2 * max_blocks))))
         self._fns = _torch_allocator() if use_torch_allocator else (_capi.ALLOC_FN(), _capi.FREE_FN())
         p = cvx_submap_params(float(voxel_size), float(trunc), float(max_weight), int(storage),
-                              int(max_blocks), int(hash_slots), int(_capi.CVX_SUBMAP_PIPELINED if pipelined else 0),
+                              int(max_blocks), int(hash_slots),
+                              int(_capi.CVX_SUBMAP_FOUR_SETS if sets == 4 else
+                                  (_capi.CVX_SUBMAP_PIPELINED if (pipelined or sets == 2) else 0)),
                               self._fns[0], self._fns[1], None, _capi._stream_handle(stream))
         self.voxel_size, self.trunc, self.max_weight, self.storage = voxel_size, trunc, max_weight, storage
         self.max_blocks, self.hash_slots = max_blocks, hash_slots

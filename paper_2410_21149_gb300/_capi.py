@@ -24,6 +24,7 @@ CVX_W_CONST, CVX_W_QUADRATIC, CVX_W_PER_POINT = 0, 1, 2
 CVX_DROP_NONE, CVX_DROP_LINEAR, CVX_DROP_QUADRATIC = 0, 1, 2
 CVX_SENSOR_PINHOLE, CVX_SENSOR_SPHERICAL = 0, 1
 CVX_SUBMAP_PIPELINED = 1
+CVX_SUBMAP_FOUR_SETS = 2
 CVX_INTEGRATE_CARVE = 1
 
 STATUS_NAMES = {0: "CVX_OK", -1: "CVX_ERR_INVALID_ARG", -2: "CVX_ERR_OOM", -3: "CVX_ERR_CAPACITY",

@@ -22,6 +22,10 @@ from . import _capi
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
     (256, 2), (256, 4), (256, 8), (256, -1), (512, 4), (512, 8), (512, -1), (1024, 4), (1024, 8), (1024, -1))
+# the batched persistent launch takes whole tiles as work items: larger tiles amortise an item's
+# dependency check and queue atomic
+BATCH_CANDIDATES: Tuple[Tuple[int, int], ...] = (
+    (256, -1), (256, 2), (512, -1), (512, 4), (1024, -1), (1024, 4), (2048, -1), (2048, 8))
 
 _lock = threading.Lock()
 
@@ -143,7 +147,7 @@ def tune_scans(voxel_size: float, trunc: float, max_weight: float, storage: int,
 
 
 def tune_batch(maps: List[int], scans: List[tuple], key_parts: str, force: bool = False,
-               candidates: Iterable[Tuple[int, int]] = DEFAULT_CANDIDATES, reset=None) -> Dict[str, float]:
+               candidates: Iterable[Tuple[int, int]] = BATCH_CANDIDATES, reset=None) -> Dict[str, float]:
     """Batched path.  maps: submap handles; scans: [(map index, points, T, pw,
     params)] whose params' pts_per_cta / local_blocks are replaced by each
     candidate; reset() clears the submaps between runs."""

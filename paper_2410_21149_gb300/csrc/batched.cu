@@ -2,7 +2,7 @@
 //
 // Scans of one submap are frames in the order given; scans of different
 // submaps are independent (submaps are separate maps, coVoxSLAM Sec. III-C).
-// One cooperative kernel works through a queue of items in dependency order,
+// One persistent kernel works through a queue of items in dependency order,
 // with no grid-wide barrier:
 //   tile item   one tile of one scan: integrate_tile (count, allocate,
 //               per-voxel sums; Sec. III-D) into the scan's per-scan set;
@@ -10,12 +10,15 @@
 //               kMergeParts-th span of the submap's allocated blocks, the
 //               blocks stamped with the scan's epoch merged into D and W.
 // An item waits (bounded) only for what it needs: a tile for the merge that
-// last used its per-scan set (pipelined submaps have two sets, so a scan's
-// tiles overlap the previous scan's merge), a merge part for all tiles of its
+// last used its per-scan set (pipelined submaps have two or four sets, so a
+// scan's tiles overlap the previous scans' merges), a merge part for all tiles of its
 // scan and for the merge of the submap's previous scan (D and W in frame
-// order).  Every item waits only on items earlier in the queue, which
-// resident CTAs hold, so the launch always progresses; a wait that runs out
-// records CVX_ERR_TIMEOUT, after which every CTA drains the queue and leaves.
+// order).  Every item waits only on items earlier in the queue, which a
+// running CTA has already taken (a CTA takes items only while it runs, and
+// the items a wait needs all precede the waiting one), so the launch always
+// progresses whether or not all its CTAs are resident at once -- an ordinary
+// launch suffices; a wait that runs out records CVX_ERR_TIMEOUT, after which
+// every CTA drains the queue and leaves.
 // Load balance is dynamic (Sec. III-D workload equalisation): each CTA takes
 // the next item as soon as it is free.  The arithmetic is the per-scan path's
 // device code, unchanged.
@@ -43,7 +46,7 @@ constexpr int kErrIncomplete = 8;                // a scan was left unmerged (on
 
 // Per scan of a launch, in queue order of its tiles.
 struct ScanMeta {
-  int view;       // index into BatchDev::views (2 * submap + per-scan set)
+  int view;       // index into BatchDev::views (4 * submap + per-scan set)
   int prev;       // previous scan of the same submap (its merge precedes this one's), or -1
   int prev_set;   // the scan whose merge frees this scan's per-scan set, or -1
   int n_tiles;
@@ -52,7 +55,7 @@ struct ScanMeta {
 };
 
 struct BatchDev {
-  const SubmapDev* views;   // [2 * n_maps]: per submap, per-scan set 0 and 1 (the same when unpipelined)
+  const SubmapDev* views;   // [4 * n_maps]: per submap, its per-scan sets 0..3 (repeated when it has fewer)
   const ScanDev* scans;     // [n_scans]
   const ScanMeta* meta;     // [n_scans]
   const int* seg_first;     // [n_segs + 1] first item of each queue segment
@@ -266,7 +269,7 @@ Layout layout(int max_maps, int max_scans) {
   Layout L;
   size_t o = 0;
   L.views = o;
-  o = align16(o + sizeof(SubmapDev) * 2 * max_maps);
+  o = align16(o + sizeof(SubmapDev) * 4 * max_maps);
   L.scans = o;
   o = align16(o + sizeof(ScanDev) * max_scans);
   L.meta = o;
@@ -436,27 +439,26 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   ScanMeta* hm = (ScanMeta*)(h + L.meta);
   int* hsf = (int*)(h + L.seg_first);
   int* hsc = (int*)(h + L.seg_code);
-  for (int q = 0; q < n_maps; ++q) {
-    hv[2 * q] = maps[q]->dev;
-    hv[2 * q + 1] = maps[q]->pipelined ? maps[q]->dev_b : maps[q]->dev;
-  }
-  // per scan (in queue order): descriptor, set, dependencies
-  std::vector<int> last_of_map(n_maps, -1), last2_of_map(n_maps, -1);
+  for (int q = 0; q < n_maps; ++q)
+    for (int k = 0; k < 4; ++k) hv[4 * q + k] = set_view(maps[q], k % maps[q]->n_sets);
+  // per scan (in queue order): descriptor, set, dependencies (the scans of
+  // each submap so far, in order: the set of scan k is k mod n_sets)
+  std::vector<std::vector<int>> of_map(n_maps);
   for (int k = 0; k < n_run; ++k) {
     const int s = order[k];
     const int q = scans[s].submap;
-    const bool two = maps[q]->pipelined;
+    const int ns = maps[q]->n_sets;
+    std::vector<int>& prior = of_map[q];
     hs[k] = sd[s];
     hs[k].epoch_add = (uint32_t)rank[s];
     ScanMeta& mt = hm[k];
-    mt.view = 2 * q + (two ? (rank[s] & 1) : 0);
-    mt.prev = last_of_map[q];
-    mt.prev_set = two ? last2_of_map[q] : last_of_map[q];
+    mt.view = 4 * q + rank[s] % ns;
+    mt.prev = prior.empty() ? -1 : prior.back();
+    mt.prev_set = (int)prior.size() >= ns ? prior[prior.size() - ns] : -1;
     mt.n_tiles = sd[s].n_tiles;
     mt.lb = lbs[s];
     mt.epoch_end = rank[s] == per_map[q] - 1 ? per_map[q] : 0;
-    last2_of_map[q] = last_of_map[q];
-    last_of_map[q] = k;
+    prior.push_back(k);
   }
   // queue segments, round by round: merges of the previous round's
   // single-set scans (their submaps' next tiles wait for them), this round's
@@ -534,17 +536,9 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
-  const int grid = std::min(per_sm * num_sms(), std::max(items, 1));
-  void* args[] = {&bd};
-  cudaError_t e;
-  COVOX_LAUNCH(kKBatched, st,
-               e = cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(kTileThreads), args,
-                                               tile_smem_bytes(lb_max), st));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return CVX_ERR_CUDA;
-  }
-  return CVX_OK;
+  const int grid = std::min(per_sm * num_sms(), std::max(items, 1));   // one wave of resident CTAs
+  COVOX_LAUNCH(kKBatched, st, kern<<<grid, kTileThreads, tile_smem_bytes(lb_max), st>>>(bd));
+  return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
 
 int32_t cvx_batch_error(cvx_batch* b) {

@@ -28,6 +28,8 @@ struct State {
   int32_t pending;      // pipelined per-scan path: set parity ^ 1 holds an unmerged scan
   uint32_t epoch;       // scans whose tiles have completed; the running scan's epoch is epoch + 1
   unsigned long long frames, valid_pts, obs, voxels_merged, blocks_touched;
+  int32_t frame_err_c;  // per-scan sets 2 and 3 of a four-set submap
+  int32_t frame_err_d;
 };
 
 // Everything a kernel needs to address one submap (passed by value).

@@ -110,11 +110,16 @@ __global__ void __launch_bounds__(kTileThreads) merge_kernel(SubmapDev m) {
 // batched launch numbers its scans st->epoch + 1, + 2, ... and closes them
 // all at its end; a pending pipelined scan was dropped before this runs).
 // Reset only: merged blocks hold zero sums, so this at most repeats zeroing.
-__global__ void discard_sums_kernel(SubmapDev a, SubmapDev b, int two_sets) {
+struct SetViews {
+  SubmapDev v[4];
+};
+
+__global__ void discard_sums_kernel(SetViews sets, int n_sets) {
+  const SubmapDev& a = sets.v[0];
   const int nb = min(a.st->n_blocks, a.max_blocks);
   const uint32_t e = a.st->epoch;
-  for (int set = 0; set <= two_sets; ++set) {
-    const SubmapDev& m = set ? b : a;
+  for (int set = 0; set < n_sets; ++set) {
+    const SubmapDev& m = sets.v[set];
     for (int p = blockIdx.x; p < nb; p += gridDim.x) {
       const uint32_t t = m.tepoch[p];
       if (t <= e) continue;
@@ -358,7 +363,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   if (p->max_blocks <= 0 || p->max_blocks > (1ll << 25)) return CVX_ERR_INVALID_ARG;
   if (p->hash_slots < 2 || (p->hash_slots & (p->hash_slots - 1)) || p->hash_slots > (1ll << 31))
     return CVX_ERR_INVALID_ARG;
-  if (p->flags & ~(int64_t)CVX_SUBMAP_PIPELINED) return CVX_ERR_INVALID_ARG;
+  if (p->flags & ~(int64_t)(CVX_SUBMAP_PIPELINED | CVX_SUBMAP_FOUR_SETS)) return CVX_ERR_INVALID_ARG;
   if (p->storage == CVX_STORE_F16 && p->max_weight > 65504.0f) return CVX_ERR_INVALID_ARG;
   if ((p->alloc == nullptr) != (p->free == nullptr)) return CVX_ERR_INVALID_ARG;
 
@@ -376,13 +381,14 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
   d.tepoch = (uint32_t*)sub_alloc(m, nb * 4);
   d.st = (State*)sub_alloc(m, sizeof(State));
-  int expect = 8;
-  m->pipelined = (p->flags & CVX_SUBMAP_PIPELINED) != 0;
-  SubmapDev& db = m->dev_b;
-  if (m->pipelined) {   // second per-scan set: sums and touch epochs
-    db.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
-    db.tepoch = (uint32_t*)sub_alloc(m, nb * 4);
-    expect = 10;
+  m->n_sets = (p->flags & CVX_SUBMAP_FOUR_SETS) ? 4 : ((p->flags & CVX_SUBMAP_PIPELINED) ? 2 : 1);
+  m->pipelined = m->n_sets > 1;
+  const int expect = 8 + 2 * (m->n_sets - 1);
+  float2* acc_x[3] = {nullptr, nullptr, nullptr};
+  uint32_t* tep_x[3] = {nullptr, nullptr, nullptr};
+  for (int k = 1; k < m->n_sets; ++k) {   // further per-scan sets: sums and touch epochs
+    acc_x[k - 1] = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
+    tep_x[k - 1] = (uint32_t*)sub_alloc(m, nb * 4);
   }
   if (m->n_allocs != expect) {
     sub_free_all(m);
@@ -398,13 +404,13 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.inv_vs = 1.0f / p->voxel_size;
   d.trunc = p->trunc;
   d.max_w = p->max_weight;
-  if (m->pipelined) {
-    float2* acc_b = db.acc;
-    uint32_t* tepoch_b = db.tepoch;
-    db = d;
-    db.acc = acc_b;
-    db.tepoch = tepoch_b;
-    db.frame_err = &d.st->frame_err_b;
+  int32_t* fe_x[3] = {&d.st->frame_err_b, &d.st->frame_err_c, &d.st->frame_err_d};
+  for (int k = 1; k < m->n_sets; ++k) {
+    SubmapDev& v = k == 1 ? m->dev_b : m->dev_cd[k - 2];
+    v = d;
+    v.acc = acc_x[k - 1];
+    v.tepoch = tep_x[k - 1];
+    v.frame_err = fe_x[k - 1];
   }
   cudaStream_t s = (cudaStream_t)p->stream;
   m->last_stream = s;
@@ -415,9 +421,9 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   cudaMemsetAsync(d.W, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
   cudaMemsetAsync(d.st, 0, sizeof(State), s);
-  if (m->pipelined) {
-    cudaMemsetAsync(db.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
-    cudaMemsetAsync(db.tepoch, 0, nb * 4, s);
+  for (int k = 1; k < m->n_sets; ++k) {
+    cudaMemsetAsync(set_view(m, k).acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
+    cudaMemsetAsync(set_view(m, k).tepoch, 0, nb * 4, s);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
@@ -495,14 +501,14 @@ cvx_status cvx_reset_submap(cvx_submap* map, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   map->last_stream = s;
   if (flush_pending(map, s, true) != CVX_OK) return CVX_ERR_CUDA;
-  COVOX_LAUNCH(kKDiscard, s,
-               discard_sums_kernel<<<num_sms(), 256, 0, s>>>(map->dev, map->dev_b, map->pipelined ? 1 : 0));
+  SetViews sv;
+  for (int k = 0; k < 4; ++k) sv.v[k] = set_view(map, k < map->n_sets ? k : 0);
+  COVOX_LAUNCH(kKDiscard, s, discard_sums_kernel<<<num_sms(), 256, 0, s>>>(sv, map->n_sets));
   const int bpb = (int)(kVoxPerBlock * map->bytes_per_vox);
   COVOX_LAUNCH(kKZeroPool, s, zero_pool_kernel<<<num_sms() * 4, 256, 0, s>>>(map->dev, bpb));
   cudaMemsetAsync(map->dev.keys, 0xff, (size_t)map->p.hash_slots * 8, s);
   cudaMemsetAsync(map->dev.vals, 0xff, (size_t)map->p.hash_slots * 4, s);
-  cudaMemsetAsync(map->dev.tepoch, 0, (size_t)map->p.max_blocks * 4, s);
-  if (map->pipelined) cudaMemsetAsync(map->dev_b.tepoch, 0, (size_t)map->p.max_blocks * 4, s);
+  for (int k = 0; k < map->n_sets; ++k) cudaMemsetAsync(set_view(map, k).tepoch, 0, (size_t)map->p.max_blocks * 4, s);
   cudaMemsetAsync(map->dev.st, 0, sizeof(State), s);
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
@@ -535,7 +541,7 @@ cvx_status cvx_submap_status(cvx_submap* map) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
-  return status_from_bits(st.sticky_err | st.frame_err | st.frame_err_b);
+  return status_from_bits(st.sticky_err | st.frame_err | st.frame_err_b | st.frame_err_c | st.frame_err_d);
 }
 
 cvx_status cvx_flush_submap(cvx_submap* map, void* stream) {

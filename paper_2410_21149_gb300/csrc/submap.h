@@ -15,6 +15,8 @@ struct cvx_submap {
   cvx_submap_params p;
   covox::SubmapDev dev;
   covox::SubmapDev dev_b;   // the second per-scan set of a pipelined submap
+  covox::SubmapDev dev_cd[2];   // the third and fourth per-scan sets of a four-set submap
+  int n_sets;               // per-scan sets: 1, 2 (pipelined) or 4
   bool pipelined;
   bool maybe_pending;       // a pipelined per-scan launch may have left a scan unmerged
   size_t bytes_per_vox;
@@ -22,11 +24,16 @@ struct cvx_submap {
   struct Alloc {
     void* ptr;
     size_t bytes;
-  } allocs[16];
+  } allocs[24];
   int n_allocs;
 };
 
 namespace covox {
+
+// The view of per-scan set k (0 .. n_sets - 1) of a submap.
+inline const SubmapDev& set_view(const cvx_submap* m, int k) {
+  return k == 0 ? m->dev : (k == 1 ? m->dev_b : m->dev_cd[k - 2]);
+}
 
 inline int num_sms() {
   static int n = 0;

@@ -97,15 +97,15 @@ def compare(gpu, orc, d_tol, w_rel=1e-4, w_floor=1e-6, fp16_trunc=None, d_tol_w=
 
 
 def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=False, pipelined=False,
-                    wave_limit=0, point_weights=None, **over):
+                    wave_limit=0, point_weights=None, sets=0, **over):
     """Integrate all submaps of the workload with one cvx_integrate_batch call
     (scans of a submap are frames in order).  Returns the run_gpu tuple list."""
     import torch
     import paper_2410_21149_gb300 as cvx
     from paper_2410_21149_gb300 import _capi
     storages = storages or [wl.storage] * len(wl.submaps)
-    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, st, max_blocks=max_blocks, pipelined=pipelined)
-            for sm, st in zip(wl.submaps, storages)]
+    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, st, max_blocks=max_blocks, pipelined=pipelined,
+                       sets=sets) for sm, st in zip(wl.submaps, storages)]
     keep = []
     scans = []
     # interleave submaps' scans (any order works; frames keep per-submap order)

@@ -21,12 +21,14 @@ def mixed():
     return sg.make_c4(n_submaps=6, max_scans=4, depth_wh=(160, 120), lidar_rc=(16, 256))
 
 
-@pytest.mark.parametrize("pipelined,wave_limit", [(False, 0), (True, 0), (True, 2)])
-def test_batched_mixed_fp32_fp16_vs_oracle(mixed, pipelined, wave_limit):
-    """Mixed storage; plain and pipelined waves (merges of one wave overlap the
-    next wave's tiles), and waves cut into chunks of two scans."""
+@pytest.mark.parametrize("pipelined,wave_limit,sets", [(False, 0, 0), (True, 0, 0), (True, 2, 0), (True, 0, 4),
+                                                        (True, 3, 4)])
+def test_batched_mixed_fp32_fp16_vs_oracle(mixed, pipelined, wave_limit, sets):
+    """Mixed storage; one, two and four per-scan sets (a scan's tiles overlap
+    the merges of the previous one or three scans of its submap), and rounds
+    cut into chunks of two or three scans."""
     storages = [m % 2 for m in range(len(mixed.submaps))]
-    g = run_gpu_batched(mixed, storages, pipelined=pipelined, wave_limit=wave_limit)
+    g = run_gpu_batched(mixed, storages, pipelined=pipelined, wave_limit=wave_limit, sets=sets)
     for m, (a, st) in enumerate(zip(g, storages)):
         sm = mixed.submaps[m]
         sub = sg.Workload(mixed.name, [sm], mixed.max_weight, mixed.weight_mode, mixed.dropoff,
@@ -78,3 +80,15 @@ def test_batched_rejects_bad_arguments():
     torch.cuda.synchronize()
     assert sub.counters()["frames"] == 0 and _capi.cvx_batch_error(b) == 0
     _capi.cvx_batch_destroy(b)
+
+
+def test_batched_single_submap_many_frames_four_sets():
+    """One submap, 12 frames in one launch (several scans of the same submap
+    in flight at once), four sets against two, one and the oracle."""
+    wl = sg.make_c2(n_frames=12, width=320, height=240)
+    o = run_oracle(wl)[0]
+    for pipelined, sets in ((True, 4), (True, 0), (False, 0)):
+        g = run_gpu_batched(wl, pipelined=pipelined, sets=sets, pts_per_cta=512, local_blocks=-1)[0]
+        compare(g, o, 1e-5)
+        assert g[3]["frames"] == 12 and g[3]["observations"] == o[3]["obs"]
+
