@@ -54,7 +54,8 @@ def lib():
             L.orc_point_obs.argtypes = [vp, vp, f32, f32, f32, f32, i32, i32, i32, f32, vp, vp, vp,
                                         i32, vp]
             L.orc_integrate.restype = i32
-            L.orc_integrate.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp, i32]
+            L.orc_integrate.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp, i32, vp]
+            L.orc_extract_colors.argtypes = [vp, vp]
             L.orc_integrate_parallel.restype = i32
             L.orc_integrate_parallel.argtypes = [vp, vp, i64, vp, vp, i32, i32, f32, f32, i32, vp, i32, i32]
             L.orc_extract.argtypes = [vp, vp, vp, vp]
@@ -89,15 +90,18 @@ class OracleSubmap:
 
     def integrate(self, points: np.ndarray, T: np.ndarray, point_weights: Optional[np.ndarray] = None,
                   weight_mode: int = 0, dropoff: int = 0, min_range: float = 0.1,
-                  max_range: float = 1e9, sensor: int = 0, carve: bool = False) -> Dict[str, int]:
+                  max_range: float = 1e9, sensor: int = 0, carve: bool = False,
+                  colors: Optional[np.ndarray] = None) -> Dict[str, int]:
         """One frame; returns the frame's counts and status (0 or -4 key range).
-        carve: traverse from the sensor origin (free-space carving)."""
+        carve: traverse from the sensor origin (free-space carving).  colors:
+        per-point RGB [n,3] fused into the voxels with the same weights."""
         pts = _f32(points).reshape(-1, 3)
         Tm = _f32(T).reshape(12)
         pw = None if point_weights is None else _f32(point_weights)
+        rgb = None if colors is None else _f32(colors).reshape(-1, 3)
         stats = np.zeros(6, dtype=np.int64)
         rc = lib().orc_integrate(self.h, _p(pts), len(pts), _p(Tm), _p(pw), weight_mode, dropoff,
-                                 min_range, max_range, sensor, _p(stats), 1 if carve else 0)
+                                 min_range, max_range, sensor, _p(stats), 1 if carve else 0, _p(rgb))
         keys = ("valid", "obs", "voxels", "blocks", "new_blocks", "key_range")
         out = dict(zip(keys, (int(x) for x in stats)))
         out["status"] = rc
@@ -125,6 +129,12 @@ class OracleSubmap:
     @property
     def num_blocks(self) -> int:
         return int(lib().orc_num_blocks(self.h))
+
+    def extract_colors(self) -> np.ndarray:
+        """Fused colours float64 [nb, 3, 512] in the order of extract()."""
+        C = np.zeros((self.num_blocks, 3, 512), dtype=np.float64)
+        lib().orc_extract_colors(self.h, _p(C))
+        return C
 
     def extract(self):
         """(keys int32 [nb,3], D float64 [nb,512], W float64 [nb,512]) sorted by key."""

@@ -18,7 +18,11 @@
  *     merged into the stored voxel as D <- (D W + S_wd) / (W + S_w),
  *     W <- min(W + S_w, max_weight);
  *   - weights are constant, 1/z^2, or given per point, optionally with a
- *     behind-surface drop-off (Sec. III-C, weighting paragraph).
+ *     behind-surface drop-off (Sec. III-C, weighting paragraph);
+ *   - with colours given per point, every voxel also fuses an RGB colour with
+ *     the same observation weights and the same merge rule,
+ *     C <- (C W + S_wc) / (W + S_w) (the "TSDF + Color" integration timed in
+ *     Sec. IV).
  *
  * Precision: distances, weights, sums and stored D/W are FP64.  The traversal
  * itself is FP32 with a fixed operation order (the same FP32 formula the CUDA
@@ -52,6 +56,7 @@ using Key = std::array<int32_t, 3>;
 struct Block {
   double D[kBlockVox];
   double W[kBlockVox];
+  double C[3][kBlockVox];   // fused RGB (zero unless scans carried colours)
 };
 
 struct Map {
@@ -236,10 +241,18 @@ struct KeyHash {
   }
 };
 
-void merge_voxel(Map* m, Block& b, int l, double swd, double sw) {
+// Per-frame sums of one voxel: weighted distance, weight, weighted colour.
+struct VoxelSums {
+  double swd = 0.0, sw = 0.0;
+  double swc[3] = {0.0, 0.0, 0.0};
+};
+
+void merge_voxel(Map* m, Block& b, int l, const VoxelSums& vs_) {
+  const double swd = vs_.swd, sw = vs_.sw;
   double W = b.W[l], D = b.D[l];
   double Wn = W + sw;
   if (!(Wn > 0)) return;
+  for (int k = 0; k < 3; ++k) b.C[k][l] = (b.C[k][l] * W + vs_.swc[k]) / Wn;
   double Dn = (D * W + swd) / Wn;
   double Wc = Wn < (double)m->max_w ? Wn : (double)m->max_w;
   if (m->fp16) {
@@ -250,17 +263,19 @@ void merge_voxel(Map* m, Block& b, int l, double swd, double sw) {
   b.W[l] = Wc;
 }
 
-using FrameSums = std::map<Key, std::pair<double, double>>;
+using FrameSums = std::map<Key, VoxelSums>;
 
 struct FrameCounts {
   int64_t valid = 0, nobs = 0, bad = 0;
 };
 
 // Observations of points [i0, i1) of one scan, summed per voxel in point
-// order into `frame` (weighted distance, weight).
+// order into `frame` (weighted distance, weight, and with rgb -- [n,3]
+// colours -- weighted colour).
 void accumulate_points(const Map* m, const float* pts, int64_t i0, int64_t i1, const float* T,
                        const float* pw, int weight_mode, int dropoff, float min_range,
-                       float max_range, int sensor, int carve, FrameSums* frame, FrameCounts* cnt) {
+                       float max_range, int sensor, int carve, const float* rgb, FrameSums* frame,
+                       FrameCounts* cnt) {
   std::vector<Key> vox;
   for (int64_t i = i0; i < i1; ++i) {
     const float* ps = pts + 3 * i;
@@ -280,8 +295,10 @@ void accumulate_points(const Map* m, const float* pts, int64_t i0, int64_t i1, c
       double d = voxel_distance(ray, v, m->vs, m->trunc);
       double w = obs_weight(base, d, m->vs, m->trunc, dropoff);
       auto& acc = (*frame)[v];
-      acc.first += w * d;
-      acc.second += w;
+      acc.swd += w * d;
+      acc.sw += w;
+      if (rgb)
+        for (int k = 0; k < 3; ++k) acc.swc[k] += w * (double)rgb[3 * i + k];
       ++cnt->nobs;
     }
   }
@@ -303,7 +320,7 @@ int apply_frame(Map* m, const FrameSums& frame, const FrameCounts& cnt, int64_t*
   if (cnt.bad == 0) {
     for (auto& kv : frame) {
       Block& blk = m->blocks[block_of(kv.first)];
-      merge_voxel(m, blk, local_of(kv.first), kv.second.first, kv.second.second);
+      merge_voxel(m, blk, local_of(kv.first), kv.second);
     }
   }
   if (stats) {
@@ -374,19 +391,20 @@ int orc_point_obs(const float* ps, const float* T, float vs, float trunc, float 
 
 
 /* Integrate one scan (one frame).  pts: [n,3] sensor frame; T: 3x4 row-major
- * submap <- sensor; pw: per-point weights (weight_mode 2) or NULL.
+ * submap <- sensor; pw: per-point weights (weight_mode 2) or NULL; rgb: per
+ * point colours [n,3] or NULL.
  * stats (optional, 6 entries): valid points, observations, unique voxels,
  * touched blocks, new blocks, key-range rejects.  Returns 0, or -4 if any point
  * left the key range (those points are skipped and, as in the CUDA path, the
  * merge of that frame is skipped while newly seen blocks stay allocated). */
 int orc_integrate(void* h, const float* pts, int64_t n, const float* T, const float* pw,
                   int weight_mode, int dropoff, float min_range, float max_range, int sensor,
-                  int64_t* stats, int carve) {
+                  int64_t* stats, int carve, const float* rgb) {
   Map* m = (Map*)h;
   FrameSums frame;   // frame sums keyed by voxel, accumulated in point-index order
   FrameCounts cnt;
   accumulate_points(m, pts, 0, n, T, pw, weight_mode, dropoff, min_range, max_range, sensor, carve,
-                    &frame, &cnt);
+                    rgb, &frame, &cnt);
   return apply_frame(m, frame, cnt, stats);
 }
 
@@ -405,15 +423,15 @@ int orc_integrate_parallel(void* h, const float* pts, int64_t n, const float* T,
   for (int t = 0; t < threads; ++t) {
     const int64_t i0 = n * t / threads, i1 = n * (t + 1) / threads;
     accumulate_points(m, pts, i0, i1, T, pw, weight_mode, dropoff, min_range, max_range, sensor,
-                      carve, &part[t], &pc[t]);
+                      carve, nullptr, &part[t], &pc[t]);
   }
   FrameSums frame = std::move(part[0]);
   FrameCounts cnt = pc[0];
   for (int t = 1; t < threads; ++t) {
     for (auto& kv : part[t]) {
       auto& acc = frame[kv.first];
-      acc.first += kv.second.first;
-      acc.second += kv.second.second;
+      acc.swd += kv.second.swd;
+      acc.sw += kv.second.sw;
     }
     cnt.valid += pc[t].valid;
     cnt.nobs += pc[t].nobs;
@@ -431,6 +449,16 @@ void orc_extract(void* h, int32_t* keys, double* D, double* W) {
     for (int k = 0; k < 3; ++k) keys[3 * q + k] = kv.first[k];
     std::memcpy(D + q * kBlockVox, kv.second.D, sizeof(double) * kBlockVox);
     std::memcpy(W + q * kBlockVox, kv.second.W, sizeof(double) * kBlockVox);
+    ++q;
+  }
+}
+
+/* Fused colours of all blocks in ascending key order: [nb, 3, 512]. */
+void orc_extract_colors(void* h, double* C) {
+  Map* m = (Map*)h;
+  int64_t q = 0;
+  for (auto& kv : m->blocks) {
+    std::memcpy(C + q * 3 * kBlockVox, kv.second.C, sizeof(double) * 3 * kBlockVox);
     ++q;
   }
 }
@@ -526,7 +554,10 @@ void orc_sampled(const float* const* scans, const int64_t* counts, const float* 
       Block tmp;  // reuse the single-voxel merge on a scratch block slot 0
       tmp.D[0] = D[q];
       tmp.W[0] = W[q];
-      merge_voxel(&m, tmp, 0, swd[q], sw[q]);
+      VoxelSums vsum;
+      vsum.swd = swd[q];
+      vsum.sw = sw[q];
+      merge_voxel(&m, tmp, 0, vsum);
       D[q] = tmp.D[0];
       W[q] = tmp.W[0];
     }
