@@ -762,9 +762,9 @@ def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain, make_sub, 
     t2 = time.perf_counter()
     N = sm.scans[0].points.shape[0]
     nf = len(Ts)
-    # every frame's per-point weights (features + network in one fused kernel
-    # per frame), then all frames in one batched persistent launch with
-    # per-point weights: the headline's path and launch shape
+    # every frame's per-point weights (features + network fused, all frames in
+    # one persistent launch), then all frames in one batched persistent launch
+    # with per-point weights: the headline's path and launch shape
     w_all = torch.empty((nf, N), dtype=torch.float32, device="cuda")
     prm = _capi.cvx_integrate_params.from_buffer_copy(params)
     prm.weight_mode = cvx.CVX_W_PER_POINT
@@ -774,8 +774,7 @@ def learned_form(wl, pts, Ts, stream, args, ws, rmse_plain, ms_plain, make_sub, 
 
     def step():
         sub.reset(stream)
-        for f in range(nf):
-            _capi.cvx_weight_model_point_weights(model.handle, pts[f], H, W, 0, wl.max_range, w_all[f], stream)
+        _capi.cvx_weight_model_point_weights_frames(model.handle, pts, nf, H, W, 0, wl.max_range, w_all, stream)
         _capi.cvx_integrate_batch(batch, [sub.handle], scans_l, stream)
 
     g = capture(step)

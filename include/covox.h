@@ -88,6 +88,17 @@ typedef void (*cvx_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
  * submap are in flight at once (same results; four times the per-scan
  * memory, 4 KB per block per set).  The per-scan path uses the first two. */
 #define CVX_SUBMAP_FOUR_SETS 2
+/* Colour submap (the "TSDF + Color" integration of Sec. IV): every voxel also
+ * holds a fused RGB colour, three float32 planes per block, and every
+ * per-scan set holds colour sums (16 bytes per voxel).  Every scan integrated
+ * into it must carry per-point colours (cvx_integrate_scan_color, or
+ * colors_rgb of a batched scan); each voxel's colour is the weighted mean of
+ * its observations' colours under the observation weights of the TSDF:
+ * C <- (C W + sum w c) / (W + sum w) in the same merge as D (W the stored
+ * weight before the merge).  A point with a non-finite colour channel is
+ * invalid (skipped, not counted).  Colours are fused in float32 in both
+ * storage modes. */
+#define CVX_SUBMAP_COLOR 4
 
 typedef struct {
   float voxel_size;      /* metres, > 0 */
@@ -96,7 +107,8 @@ typedef struct {
   int32_t storage;       /* cvx_storage */
   int64_t max_blocks;    /* block pool capacity (blocks of 512 voxels) */
   int64_t hash_slots;    /* hash table slots, a power of two >= 2 * max_blocks advised */
-  int64_t flags;         /* 0, CVX_SUBMAP_PIPELINED or CVX_SUBMAP_FOUR_SETS */
+  int64_t flags;         /* 0 or CVX_SUBMAP_PIPELINED or CVX_SUBMAP_FOUR_SETS, each optionally
+                            with CVX_SUBMAP_COLOR */
   cvx_alloc_fn alloc;
   cvx_free_fn free;
   void* alloc_ctx;
@@ -153,6 +165,21 @@ cvx_status cvx_create_submap(const cvx_submap_params* params, cvx_submap** out);
 cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t n,
                               const float T_sub_sensor[12], const float* point_weights,
                               const cvx_integrate_params* params, void* stream);
+
+/* cvx_integrate_scan with per-point colours (colour submaps, which require
+ * them; any other submap returns CVX_ERR_INVALID_ARG).  colors_rgb: device
+ * float32 [n,3], any units (typically [0,1]).  Colour scans run the general
+ * tile form with L2 vector reductions (params->local_blocks is ignored). */
+cvx_status cvx_integrate_scan_color(cvx_submap* map, const float* points_xyz, int64_t n,
+                                    const float T_sub_sensor[12], const float* point_weights,
+                                    const float* colors_rgb, const cvx_integrate_params* params, void* stream);
+
+/* Copy out the fused colours of a colour submap: rgb float32 [capacity,3,512]
+ * (block, channel, voxel), device or host memory, the blocks in the order of
+ * cvx_extract_blocks; min(n_blocks, capacity) blocks are copied and counted
+ * in *n_out.  With rgb == NULL only *n_out (the number of blocks) is written.
+ * CVX_ERR_INVALID_ARG for a submap without colour.  Synchronises `stream`. */
+cvx_status cvx_extract_colors(cvx_submap* map, int64_t capacity, float* rgb, int64_t* n_out, void* stream);
 
 /* Copy out the allocated blocks in allocation order.  Two-call convention:
  * with keys == NULL only *n_out (the number of blocks) is written.  Otherwise
@@ -276,6 +303,7 @@ typedef struct {
   float T_sub_sensor[12];
   const float* point_weights;
   cvx_integrate_params params;
+  const float* colors_rgb;  /* device float32 [n,3] for colour submaps, else NULL */
 } cvx_scan_desc;
 
 typedef struct cvx_batch cvx_batch;
@@ -366,6 +394,12 @@ cvx_status cvx_weight_model_infer(cvx_weight_model* model, const float* features
 cvx_status cvx_weight_model_point_weights(cvx_weight_model* model, const float* points_xyz, int32_t height,
                                           int32_t width, int32_t sensor, float max_range, float* weights,
                                           void* stream);
+/* The same for n_frames organised scans of one shape in one persistent
+ * launch: points_xyz device float32 [n_frames, height*width, 3], weights
+ * device float32 [n_frames, height*width] (frame-major). */
+cvx_status cvx_weight_model_point_weights_frames(cvx_weight_model* model, const float* points_xyz,
+                                                 int32_t n_frames, int32_t height, int32_t width, int32_t sensor,
+                                                 float max_range, float* weights, void* stream);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr; lr = 0 only
  * computes the gradient) on the mean over points with mask != 0 of
  * w e2 - ln w (Gaussian negative log likelihood of precision w).  The

@@ -22,7 +22,8 @@
  *   - with colours given per point, every voxel also fuses an RGB colour with
  *     the same observation weights and the same merge rule,
  *     C <- (C W + S_wc) / (W + S_w) (the "TSDF + Color" integration timed in
- *     Sec. IV).
+ *     Sec. IV); a point with a non-finite colour channel is invalid, like one
+ *     with an unusable per-point weight.
  *
  * Precision: distances, weights, sums and stored D/W are FP64.  The traversal
  * itself is FP32 with a fixed operation order (the same FP32 formula the CUDA
@@ -209,6 +210,12 @@ bool point_weight_ok(const float* pw, int64_t i, int weight_mode) {
   return std::isfinite(w) && w >= 0.0f;
 }
 
+// With colours, a point is usable only if all three channels are finite.
+bool point_colour_ok(const float* rgb, int64_t i) {
+  if (!rgb) return true;
+  return std::isfinite(rgb[3 * i]) && std::isfinite(rgb[3 * i + 1]) && std::isfinite(rgb[3 * i + 2]);
+}
+
 double base_weight(const float* ps, const Ray& ray, const float* pw, int64_t i, int weight_mode,
                    int sensor) {
   if (weight_mode == 0) return 1.0;
@@ -282,6 +289,7 @@ void accumulate_points(const Map* m, const float* pts, int64_t i0, int64_t i1, c
     Ray ray;
     if (!make_ray(ps, T, min_range, max_range, sensor, &ray)) continue;
     if (!point_weight_ok(pw, i, weight_mode)) continue;
+    if (!point_colour_ok(rgb, i)) continue;
     float A[3], B[3];
     if (!band_segment(ray, m->trunc, m->vs, A, B, carve != 0)) {
       ++cnt->bad;

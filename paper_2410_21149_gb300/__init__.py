@@ -53,20 +53,22 @@ class Submap:
     def __init__(self, voxel_size: float, trunc: float, max_weight: float = 1e4,
                  storage: int = CVX_STORE_F32, max_blocks: int = 1 << 16,
                  hash_slots: Optional[int] = None,
-                 use_torch_allocator: bool = True, stream=None, pipelined: bool = False, sets: int = 0):
+                 use_torch_allocator: bool = True, stream=None, pipelined: bool = False, sets: int = 0,
+                 color: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("Submap needs a CUDA device; there is no CPU path")
         if hash_slots is None:
             hash_slots = 1 << max(1, int(np.ceil(np.log2(2 * max_blocks))))
         self._fns = _torch_allocator() if use_torch_allocator else (_capi.ALLOC_FN(), _capi.FREE_FN())
+        flags = (_capi.CVX_SUBMAP_FOUR_SETS if sets == 4 else
+                 (_capi.CVX_SUBMAP_PIPELINED if (pipelined or sets == 2) else 0))
+        flags |= _capi.CVX_SUBMAP_COLOR if color else 0
         p = cvx_submap_params(float(voxel_size), float(trunc), float(max_weight), int(storage),
-                              int(max_blocks), int(hash_slots),
-                              int(_capi.CVX_SUBMAP_FOUR_SETS if sets == 4 else
-                                  (_capi.CVX_SUBMAP_PIPELINED if (pipelined or sets == 2) else 0)),
+                              int(max_blocks), int(hash_slots), int(flags),
                               self._fns[0], self._fns[1], None, _capi._stream_handle(stream))
         self.voxel_size, self.trunc, self.max_weight, self.storage = voxel_size, trunc, max_weight, storage
-        self.max_blocks, self.hash_slots = max_blocks, hash_slots
+        self.max_blocks, self.hash_slots, self.color = max_blocks, hash_slots, color
         self.handle = _capi.cvx_create_submap(p)
 
     def close(self):
@@ -81,8 +83,13 @@ class Submap:
             pass
 
     def integrate(self, points, T_sub_sensor, params: cvx_integrate_params, point_weights=None,
-                  stream=None) -> None:
-        _capi.cvx_integrate_scan(self.handle, points, T_sub_sensor, point_weights, params, stream)
+                  stream=None, colors=None) -> None:
+        """colors: CUDA float32 [n,3] per-point colours (required by colour submaps)."""
+        if colors is None:
+            _capi.cvx_integrate_scan(self.handle, points, T_sub_sensor, point_weights, params, stream)
+        else:
+            _capi.cvx_integrate_scan_color(self.handle, points, T_sub_sensor, point_weights, colors, params,
+                                           stream)
 
     def reset(self, stream=None) -> None:
         _capi.cvx_reset_submap(self.handle, stream)
@@ -124,3 +131,11 @@ class Submap:
         W = torch.empty((max(nb, 1), 512), dtype=dt, device="cuda")
         n = _capi.cvx_extract_blocks(self.handle, nb, keys, D, W, stream)
         return keys[:n], D[:n], W[:n]
+
+    def extract_colors(self, stream=None):
+        """Fused colours [nb, 3, 512] float32 CUDA tensor, blocks in extract() order."""
+        import torch
+        nb = _capi.cvx_extract_colors(self.handle, 0, None, stream)
+        C = torch.empty((max(nb, 1), 3, 512), dtype=torch.float32, device="cuda")
+        n = _capi.cvx_extract_colors(self.handle, nb, C, stream)
+        return C[:n]

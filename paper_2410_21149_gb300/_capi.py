@@ -25,6 +25,7 @@ CVX_DROP_NONE, CVX_DROP_LINEAR, CVX_DROP_QUADRATIC = 0, 1, 2
 CVX_SENSOR_PINHOLE, CVX_SENSOR_SPHERICAL = 0, 1
 CVX_SUBMAP_PIPELINED = 1
 CVX_SUBMAP_FOUR_SETS = 2
+CVX_SUBMAP_COLOR = 4
 CVX_INTEGRATE_CARVE = 1
 
 STATUS_NAMES = {0: "CVX_OK", -1: "CVX_ERR_INVALID_ARG", -2: "CVX_ERR_OOM", -3: "CVX_ERR_CAPACITY",
@@ -66,7 +67,8 @@ class cvx_counters(ctypes.Structure):
 class cvx_scan_desc(ctypes.Structure):
     _fields_ = [("submap", ctypes.c_int32), ("pad", ctypes.c_int32), ("points_xyz", ctypes.c_void_p),
                 ("n", ctypes.c_int64), ("T_sub_sensor", ctypes.c_float * 12),
-                ("point_weights", ctypes.c_void_p), ("params", cvx_integrate_params)]
+                ("point_weights", ctypes.c_void_p), ("params", cvx_integrate_params),
+                ("colors_rgb", ctypes.c_void_p)]
 
 
 class cvx_submap_view(ctypes.Structure):
@@ -89,7 +91,9 @@ SIGNATURES = {
     "cvx_version": (ctypes.c_char_p, []),
     "cvx_create_submap": (_i32, [ctypes.POINTER(cvx_submap_params), ctypes.POINTER(_vp)]),
     "cvx_integrate_scan": (_i32, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(cvx_integrate_params), _vp]),
+    "cvx_integrate_scan_color": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, ctypes.POINTER(cvx_integrate_params), _vp]),
     "cvx_extract_blocks": (_i32, [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64), _vp]),
+    "cvx_extract_colors": (_i32, [_vp, _i64, _vp, ctypes.POINTER(_i64), _vp]),
     "cvx_reset_submap": (_i32, [_vp, _vp]),
     "cvx_submap_status": (_i32, [_vp]),
     "cvx_flush_submap": (_i32, [_vp, _vp]),
@@ -119,6 +123,7 @@ SIGNATURES = {
     "cvx_weight_model_params": (_i32, [_vp, _vp, _vp, _vp]),
     "cvx_weight_model_infer": (_i32, [_vp, _vp, _i64, _vp, _vp]),
     "cvx_weight_model_point_weights": (_i32, [_vp, _vp, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
+    "cvx_weight_model_point_weights_frames": (_i32, [_vp, _vp, _i32, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "cvx_weight_model_train_step": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, _vp]),
     "cvx_weight_model_last": (_i32, [_vp, _vp, _vp, _vp]),
     "cvx_weight_model_destroy": (None, [_vp]),
@@ -190,6 +195,24 @@ def cvx_integrate_scan(handle: int, points, T_sub_sensor, point_weights, params:
                                    ctypes.byref(params), _stream_handle(stream)), "cvx_integrate_scan")
 
 
+def cvx_integrate_scan_color(handle: int, points, T_sub_sensor, point_weights, colors,
+                             params: cvx_integrate_params, stream=None) -> None:
+    n = int(points.shape[0])
+    pp = _dev_ptr(points, "torch.float32", "points") if n else None
+    pw = None if point_weights is None else _dev_ptr(point_weights, "torch.float32", "point_weights")
+    pc = _dev_ptr(colors, "torch.float32", "colors") if n else None
+    T = np.ascontiguousarray(T_sub_sensor, dtype=np.float32).reshape(12)
+    check(lib().cvx_integrate_scan_color(handle, pp, n, T.ctypes.data_as(ctypes.c_void_p), pw, pc,
+                                         ctypes.byref(params), _stream_handle(stream)), "cvx_integrate_scan_color")
+
+
+def cvx_extract_colors(handle: int, capacity: int, rgb, stream=None) -> int:
+    n = ctypes.c_int64(0)
+    check(lib().cvx_extract_colors(handle, capacity, None if rgb is None else rgb.data_ptr(), ctypes.byref(n),
+                                   _stream_handle(stream)), "cvx_extract_colors")
+    return n.value
+
+
 def cvx_batch_create(max_submaps: int, max_scans: int) -> int:
     h = ctypes.c_void_p()
     check(lib().cvx_batch_create(max_submaps, max_scans, ctypes.byref(h)), "cvx_batch_create")
@@ -198,11 +221,15 @@ def cvx_batch_create(max_submaps: int, max_scans: int) -> int:
 
 def cvx_integrate_batch(batch: int, maps, scans, stream=None) -> None:
     """maps: submap handles; scans: list of (submap index, points tensor,
-    T (12 floats), point_weights tensor or None, cvx_integrate_params)."""
+    T (12 floats), point_weights tensor or None, cvx_integrate_params[,
+    colours tensor [n,3] for colour submaps])."""
     arr_maps = (ctypes.c_void_p * len(maps))(*maps)
     descs = (cvx_scan_desc * max(len(scans), 1))()
-    for k, (mi, pts, T, pw, prm) in enumerate(scans):
+    for k, sc in enumerate(scans):
+        mi, pts, T, pw, prm = sc[:5]
+        col = sc[5] if len(sc) > 5 else None
         n = int(pts.shape[0])
+        descs[k].colors_rgb = None if col is None or n == 0 else _dev_ptr(col, "torch.float32", "colors")
         descs[k].submap = int(mi)
         descs[k].points_xyz = _dev_ptr(pts, "torch.float32", "points") if n else None
         descs[k].n = n
@@ -438,6 +465,19 @@ def cvx_weight_model_point_weights(model: int, points, height: int, width: int, 
                                                int(width), int(sensor), float(max_range),
                                                _dev_ptr(weights_out, "torch.float32", "weights"),
                                                _stream_handle(stream)), "cvx_weight_model_point_weights")
+
+
+def cvx_weight_model_point_weights_frames(model: int, points, n_frames: int, height: int, width: int, sensor: int,
+                                          max_range: float, weights_out, stream=None):
+    """points: CUDA float32 [n_frames, height*width, 3] (or flat); weights_out [n_frames, height*width]."""
+    if points.numel() != 3 * n_frames * height * width or weights_out.numel() != n_frames * height * width:
+        raise ValueError("points / weights do not hold n_frames scans of height x width")
+    check(lib().cvx_weight_model_point_weights_frames(model, _dev_ptr(points, "torch.float32", "points"),
+                                                      int(n_frames), int(height), int(width), int(sensor),
+                                                      float(max_range),
+                                                      _dev_ptr(weights_out, "torch.float32", "weights"),
+                                                      _stream_handle(stream)),
+          "cvx_weight_model_point_weights_frames")
 
 
 def cvx_weight_model_train_step(model: int, features, e2, mask, lr: float, stream=None):

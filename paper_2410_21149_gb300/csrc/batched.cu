@@ -123,6 +123,7 @@ __device__ __forceinline__ unsigned long long cta_sum_b(unsigned long long v, un
 // Merge part `part` of scan s: spans part, part + kMergeParts, ... of the
 // submap's allocated blocks (blocks the submap's next scan allocates
 // meanwhile carry other epochs, so any count read now covers this scan's).
+template <bool kColour>
 __device__ void merge_part(const BatchDev& b, int s, int part, SpanList* sl, unsigned long long* red) {
   const SubmapDev& m = b.views[b.meta[s].view];
   const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
@@ -131,7 +132,7 @@ __device__ void merge_part(const BatchDev& b, int s, int part, SpanList* sl, uns
   unsigned long long merged = 0, touched = 0;
   for (int span = part; span * kSpanBlocks < nb; span += kMergeParts) {
     int t = 0;
-    merged += merge_span(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl, &t);
+    merged += merge_span<kColour>(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl, &t);
     touched += t;
   }
   const unsigned long long c = cta_sum_b(merged, red);
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) batched_kernel(BatchDev b) {
         if (!wait_at_least(b, merged_flag(b, sm.prev), 1, &ok_smem)) continue;
         seen_merged = sm.prev;
       }
-      merge_part(b, s, part, &span, red);
+      merge_part<(kVariant < 0)>(b, s, part, &span, red);
       if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(merge_ticket(b, s), 1) == kMergeParts - 1) {
@@ -390,7 +391,8 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     const cvx_scan_desc& d = scans[s];
     if (d.submap < 0 || d.submap >= n_maps) return CVX_ERR_INVALID_ARG;
     const cvx_status v =
-        make_scan_dev(maps[d.submap], d.points_xyz, d.n, d.T_sub_sensor, d.point_weights, &d.params, &sd[s], &lbs[s]);
+        make_scan_dev(maps[d.submap], d.points_xyz, d.n, d.T_sub_sensor, d.point_weights, &d.params, &sd[s], &lbs[s],
+                      d.colors_rgb);
     if (v != CVX_OK) return v;
     if (d.n == 0) continue;
     rank[s] = per_map[d.submap]++;
@@ -525,7 +527,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   // one variant for every scan: a kernel holding only that code
   int variant = -2;
   for (int k = 0; k < n_run; ++k) {
-    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff, sd[order[k]].carve || sd[order[k]].long_band);
+    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff, general_form(sd[order[k]]));
     variant = variant == -2 ? v : (variant == v ? v : -1);
   }
   const BatchedFn kern = kBatched[variant + 1];

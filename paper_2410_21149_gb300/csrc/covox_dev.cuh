@@ -42,6 +42,9 @@ struct SubmapDev {
   float2* acc;                // [max_blocks,512] per-scan sums (sum w (d - trunc), sum w), zero between scans
   uint32_t* tepoch;           // [max_blocks] epoch of the last scan of this per-scan set that touched the
                               // block: the scan's touched blocks are those holding its epoch
+  float4* cacc;               // colour submaps: [max_blocks,512] per-scan colour sums (sum w r, sum w g,
+                              // sum w b, 0) of this set, zero between scans; nullptr otherwise
+  float* C;                   // colour submaps: [max_blocks,3,512] fused RGB planes; nullptr otherwise
   State* st;
   int32_t* frame_err;         // error bits of this per-scan set (&st->frame_err or _b)
   uint32_t slot_mask;
@@ -57,6 +60,7 @@ struct SubmapDev {
 struct ScanDev {
   const float* pts;      // [n,3] sensor frame
   const float* pw;       // [n] per-point weights or nullptr
+  const float* rgb;      // [n,3] per-point colours (colour submaps) or nullptr
   long long n;
   float T[12];           // submap <- sensor, row-major 3x4
   float min_range, max_range;
@@ -222,6 +226,16 @@ __device__ __forceinline__ float base_weight(const ScanDev& sc, long long i, con
 // point is invalid (skipped like a point without a return).
 __device__ __forceinline__ bool weight_ok(const ScanDev& sc, float w0) {
   return sc.weight_mode != 2 || (isfinite(w0) && w0 >= 0.0f);
+}
+
+// A given colour must be finite in all three channels; otherwise the point is
+// invalid, as for a per-point weight.
+__device__ __forceinline__ bool colour_ok(const ScanDev& sc, long long i, float c[3]) {
+  if (!sc.rgb) return true;
+  c[0] = __ldg(sc.rgb + 3 * i);
+  c[1] = __ldg(sc.rgb + 3 * i + 1);
+  c[2] = __ldg(sc.rgb + 3 * i + 2);
+  return isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]);
 }
 
 __device__ __forceinline__ float dropoff_weight(float w, float d, float vs, float trunc, int mode) {

@@ -125,18 +125,26 @@ __global__ void discard_sums_kernel(SetViews sets, int n_sets) {
       if (t <= e) continue;
       float4* acc = reinterpret_cast<float4*>(m.acc + (size_t)p * kVoxPerBlock);
       for (int q = threadIdx.x; q < kVoxPerBlock / 2; q += blockDim.x) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m.cacc)
+        for (int q = threadIdx.x; q < kVoxPerBlock; q += blockDim.x)
+          m.cacc[(size_t)p * kVoxPerBlock + q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
 }
 
-// Zero the allocated part of the pool (reset).
+// Zero the allocated part of the pool (reset), colour planes included.
 __global__ void zero_pool_kernel(SubmapDev m, int bytes_per_block) {
-  const long long nbytes = (long long)min(m.st->n_blocks, m.max_blocks) * bytes_per_block;
-  const long long n16 = nbytes / 16;
+  const long long nb = min(m.st->n_blocks, m.max_blocks);
+  const long long n16 = nb * bytes_per_block / 16;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n16; q += stride) {
     reinterpret_cast<uint4*>(m.D)[q] = make_uint4(0, 0, 0, 0);
     reinterpret_cast<uint4*>(m.W)[q] = make_uint4(0, 0, 0, 0);
+  }
+  if (m.C) {
+    const long long c16 = nb * 3 * kVoxPerBlock * 4 / 16;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < c16; q += stride)
+      reinterpret_cast<uint4*>(m.C)[q] = make_uint4(0, 0, 0, 0);
   }
 }
 
@@ -147,6 +155,7 @@ __device__ __forceinline__ SubmapDev pick_set(const SubmapDev& a, const SubmapDe
   SubmapDev m = a;
   if (which) {
     m.acc = b.acc;
+    m.cacc = b.cacc;
     m.tepoch = b.tepoch;
     m.frame_err = b.frame_err;
   }
@@ -156,12 +165,14 @@ __device__ __forceinline__ SubmapDev pick_set(const SubmapDev& a, const SubmapDe
 // Merge the blocks of set m stamped with epoch ep among the first nb pool
 // indices: spans first, first + step, ... (256-thread CTA).  Adds the merged
 // voxels and touched blocks to the submap's counters.
+template <bool kColour = true>
 __device__ __noinline__ void merge_set(const SubmapDev& m, int nb, uint32_t ep, bool skip, int first, int step,
                                        SpanList* sl, unsigned long long* red) {
   unsigned long long merged = 0, touched = 0;
   for (int span = first; span * kSpanBlocks < nb; span += step) {
     int t = 0;
-    merged += merge_span(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl, &t);
+    merged += merge_span<kColour>(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl,
+                                  &t);
     touched += t;
   }
   const unsigned long long sum = cta_sum(merged, red);
@@ -238,7 +249,7 @@ __global__ void __launch_bounds__(kTileThreads, 5) integrate_pipelined_kernel(Su
   const int nb = min(*((volatile int32_t*)&a.st->n_blocks), a.max_blocks);
   const bool skip = *((volatile int32_t*)prev.frame_err) != 0;
   const uint32_t ep = *((volatile uint32_t*)&a.st->epoch);   // the previous scan's epoch
-  merge_set(prev, nb, ep, skip, (int)blockIdx.x - sc.n_tiles, n_merge, &sl, red);
+  merge_set<(kVariant < 0)>(prev, nb, ep, skip, (int)blockIdx.x - sc.n_tiles, n_merge, &sl, red);
 }
 
 // One thread, after integrate_pipelined_kernel: close the frame it merged
@@ -363,7 +374,8 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   if (p->max_blocks <= 0 || p->max_blocks > (1ll << 25)) return CVX_ERR_INVALID_ARG;
   if (p->hash_slots < 2 || (p->hash_slots & (p->hash_slots - 1)) || p->hash_slots > (1ll << 31))
     return CVX_ERR_INVALID_ARG;
-  if (p->flags & ~(int64_t)(CVX_SUBMAP_PIPELINED | CVX_SUBMAP_FOUR_SETS)) return CVX_ERR_INVALID_ARG;
+  if (p->flags & ~(int64_t)(CVX_SUBMAP_PIPELINED | CVX_SUBMAP_FOUR_SETS | CVX_SUBMAP_COLOR))
+    return CVX_ERR_INVALID_ARG;
   if (p->storage == CVX_STORE_F16 && p->max_weight > 65504.0f) return CVX_ERR_INVALID_ARG;
   if ((p->alloc == nullptr) != (p->free == nullptr)) return CVX_ERR_INVALID_ARG;
 
@@ -383,12 +395,19 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.st = (State*)sub_alloc(m, sizeof(State));
   m->n_sets = (p->flags & CVX_SUBMAP_FOUR_SETS) ? 4 : ((p->flags & CVX_SUBMAP_PIPELINED) ? 2 : 1);
   m->pipelined = m->n_sets > 1;
-  const int expect = 8 + 2 * (m->n_sets - 1);
+  m->colour = (p->flags & CVX_SUBMAP_COLOR) != 0;
+  const int expect = 8 + 2 * (m->n_sets - 1) + (m->colour ? 1 + m->n_sets : 0);
   float2* acc_x[3] = {nullptr, nullptr, nullptr};
   uint32_t* tep_x[3] = {nullptr, nullptr, nullptr};
+  float4* cacc_x[4] = {nullptr, nullptr, nullptr, nullptr};
   for (int k = 1; k < m->n_sets; ++k) {   // further per-scan sets: sums and touch epochs
     acc_x[k - 1] = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
     tep_x[k - 1] = (uint32_t*)sub_alloc(m, nb * 4);
+  }
+  if (m->colour) {   // RGB planes, and colour sums per per-scan set
+    d.C = (float*)sub_alloc(m, nb * 3 * kVoxPerBlock * sizeof(float));
+    for (int k = 0; k < m->n_sets; ++k) cacc_x[k] = (float4*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float4));
+    d.cacc = cacc_x[0];
   }
   if (m->n_allocs != expect) {
     sub_free_all(m);
@@ -409,6 +428,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
     SubmapDev& v = k == 1 ? m->dev_b : m->dev_cd[k - 2];
     v = d;
     v.acc = acc_x[k - 1];
+    v.cacc = cacc_x[k];
     v.tepoch = tep_x[k - 1];
     v.frame_err = fe_x[k - 1];
   }
@@ -425,6 +445,10 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
     cudaMemsetAsync(set_view(m, k).acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
     cudaMemsetAsync(set_view(m, k).tepoch, 0, nb * 4, s);
   }
+  if (m->colour) {
+    cudaMemsetAsync(d.C, 0, nb * 3 * kVoxPerBlock * sizeof(float), s);
+    for (int k = 0; k < m->n_sets; ++k) cudaMemsetAsync(cacc_x[k], 0, nb * kVoxPerBlock * sizeof(float4), s);
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     sub_free_all(m);
@@ -435,12 +459,14 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   return CVX_OK;
 }
 
-cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t n,
-                              const float T_sub_sensor[12], const float* point_weights,
-                              const cvx_integrate_params* ip, void* stream) {
+namespace {
+
+cvx_status integrate_scan(cvx_submap* map, const float* points_xyz, int64_t n, const float T_sub_sensor[12],
+                          const float* point_weights, const float* colors_rgb, const cvx_integrate_params* ip,
+                          void* stream) {
   ScanDev sc;
   int lb = 0;
-  const cvx_status v = make_scan_dev(map, points_xyz, n, T_sub_sensor, point_weights, ip, &sc, &lb);
+  const cvx_status v = make_scan_dev(map, points_xyz, n, T_sub_sensor, point_weights, ip, &sc, &lb, colors_rgb);
   if (v != CVX_OK) return v;
   cudaStream_t s = (cudaStream_t)stream;
   map->last_stream = s;
@@ -449,7 +475,7 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
   if (kernel_attributes() != CVX_OK) return CVX_ERR_CUDA;
   if (map->pipelined) {
     const int n_merge = num_sms();
-    const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff, sc.carve || sc.long_band) + 1];
+    const PipelinedFn pf = kPipelined[tile_variant(lb, sc.dropoff, general_form(sc)) + 1];
     COVOX_LAUNCH(kKPipelined, s,
                  pf<<<n_merge + sc.n_tiles, kTileThreads, smem, s>>>(map->dev, map->dev_b, sc, lb, n_merge));
     COVOX_LAUNCH(kKPipeClose, s, pipe_close_kernel<<<1, 1, 0, s>>>(map->dev, map->dev_b));
@@ -457,11 +483,53 @@ cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t 
     map->maybe_pending = true;
     return CVX_OK;
   }
-  const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff, sc.carve || sc.long_band) + 1];
+  const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff, general_form(sc)) + 1];
   COVOX_LAUNCH(kKAccum, s, fn<<<sc.n_tiles, kTileThreads, smem, s>>>(map->dev, sc, lb));
   const int grid = std::min<int>((map->dev.max_blocks + kSpanBlocks - 1) / kSpanBlocks, num_sms() * 2);
   COVOX_LAUNCH(kKMerge, s, merge_kernel<<<grid, kTileThreads, 0, s>>>(map->dev));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
+}
+
+}  // namespace
+
+cvx_status cvx_integrate_scan(cvx_submap* map, const float* points_xyz, int64_t n,
+                              const float T_sub_sensor[12], const float* point_weights,
+                              const cvx_integrate_params* ip, void* stream) {
+  return integrate_scan(map, points_xyz, n, T_sub_sensor, point_weights, nullptr, ip, stream);
+}
+
+cvx_status cvx_integrate_scan_color(cvx_submap* map, const float* points_xyz, int64_t n,
+                                    const float T_sub_sensor[12], const float* point_weights,
+                                    const float* colors_rgb, const cvx_integrate_params* ip, void* stream) {
+  return integrate_scan(map, points_xyz, n, T_sub_sensor, point_weights, colors_rgb, ip, stream);
+}
+
+cvx_status cvx_extract_colors(cvx_submap* map, int64_t capacity, float* rgb, int64_t* n_out, void* stream) {
+  if (!map || !n_out || capacity < 0 || !map->colour) return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (flush_pending(map, s, false) != CVX_OK) return CVX_ERR_CUDA;
+  int32_t nb = 0;
+  if (cudaMemcpyAsync(&nb, &map->dev.st->n_blocks, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  nb = std::min<int32_t>(nb, map->dev.max_blocks);
+  if (!rgb) {
+    *n_out = nb;
+    return CVX_OK;
+  }
+  const int64_t n = std::min<int64_t>(nb, capacity);
+  *n_out = n;
+  if (n == 0) return CVX_OK;
+  if (cudaMemcpyAsync(rgb, map->dev.C, (size_t)n * 3 * kVoxPerBlock * sizeof(float), cudaMemcpyDefault, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  return CVX_OK;
 }
 
 cvx_status cvx_extract_blocks(cvx_submap* map, int64_t capacity, int32_t* keys, void* dist,

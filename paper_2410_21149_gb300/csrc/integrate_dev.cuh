@@ -84,6 +84,11 @@ __device__ __forceinline__ void red_add2(float2* addr, float a, float b) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
 }
 
+__device__ __forceinline__ void red_add4(float4* addr, float a, float b, float c) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(0.0f)
+               : "memory");
+}
+
 // Pool index of an already activated block (read-only probe), or -1.
 __device__ __forceinline__ int find_pool(const SubmapDev& m, unsigned long long key) {
   const int s = hash_find(m, key);
@@ -358,6 +363,8 @@ __device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& 
     if (!make_ray(sc, i, r)) continue;
     const float w0 = base_weight(sc, i, r);
     if (!weight_ok(sc, w0)) continue;
+    float col[3] = {0.0f, 0.0f, 0.0f};
+    if (!colour_ok(sc, i, col)) continue;
     float A[3], B[3];
     if (!band(r, m.trunc, m.inv_vs, A, B, kCarve)) {
       atomicOr(m.frame_err, kErrKeyRange);
@@ -399,6 +406,7 @@ __device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& 
         fixed_add(t.lo_w + e, t.hi_w + e, fx.S, __float2ll_rn(w * fx.scale));
       } else if (gpool >= 0) {
         red_add2(m.acc + (size_t)gpool * kVoxPerBlock + l, w * (dc - m.trunc), w);
+        if (sc.rgb) red_add4(m.cacc + (size_t)gpool * kVoxPerBlock + l, w * col[0], w * col[1], w * col[2]);
       }
       if (d.left == 0) break;
       // next axis: the traversal rule of Dda::step, as selects
@@ -812,16 +820,18 @@ __device__ inline void integrate_tile_d(const SubmapDev& m, const ScanDev& sc, i
 // Any scan: accumulation mode, drop-off and form chosen at run time (carved
 // rays and very long bands take the general per-thread form, whose extra
 // registers the plain variants need not hold).
+// Colour scans (sc.rgb) take the general form in the L2 accumulation mode
+// (their host descriptors carry lb == 0).
 __device__ inline void integrate_tile(const SubmapDev& m, const ScanDev& sc, int tile, char* smem, int lb) {
   if (sc.carve) integrate_tile_c<true>(m, sc, tile, smem, lb);
-  else if (sc.long_band) integrate_tile_c<false>(m, sc, tile, smem, lb);
+  else if (sc.long_band || sc.rgb) integrate_tile_c<false>(m, sc, tile, smem, lb);
   else if (lb > 0) integrate_tile_d<true>(m, sc, tile, smem, lb);
   else integrate_tile_d<false>(m, sc, tile, smem, lb);
 }
 
 // Variant index of a scan: accumulation mode x drop-off (0..5), so a launch
 // whose scans share one variant runs a kernel holding only that code.
-// general: carving or bands longer than 512 cells per axis.
+// general: carving, bands longer than 512 cells per axis, or colours.
 __host__ __device__ inline int tile_variant(int lb, int dropoff, int general) {
   return general ? -1 : (lb > 0 ? 3 : 0) + dropoff;   // -1: the run-time dispatching kernel
 }
@@ -936,11 +946,53 @@ __device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, b
   return merged;
 }
 
+// Colour update of this thread's 4 voxels of block `pool` (colour submaps),
+// run before the block's D/W merge by the same thread: C <- (C W + S_wc) /
+// (W + S_w) wherever S_w != 0, W being the stored weight before the merge
+// (the same rule as D); the block's colour sums are cleared.  skip: clear only.
+template <int kStore>
+__device__ __forceinline__ void merge_colour(const SubmapDev& m, int pool, bool skip, int tid) {
+  const size_t e = (size_t)pool * kVoxPerBlock + 4 * tid;
+  const float4* a = reinterpret_cast<const float4*>(m.acc + e);
+  const float4 a0 = __ldcg(a), a1 = __ldcg(a + 1);
+  const float sw[4] = {a0.y, a0.w, a1.y, a1.w};
+  if (sw[0] == 0.f && sw[1] == 0.f && sw[2] == 0.f && sw[3] == 0.f) return;   // its colour sums are zero too
+  float4* cs = m.cacc + e;
+  if (!skip) {
+    float4 s[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[q] = __ldcg(cs + q);
+    float D[4], W[4];
+    Vox4<kStore>::load(m, e, D, W);
+    float* cp = m.C + (size_t)pool * 3 * kVoxPerBlock + 4 * tid;
+    float4 c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = __ldcg(reinterpret_cast<const float4*>(cp + k * kVoxPerBlock));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (sw[q] == 0.f) continue;
+      const float wn = W[q] + sw[q];
+      float* r = reinterpret_cast<float*>(&c[0]) + q;
+      float* g = reinterpret_cast<float*>(&c[1]) + q;
+      float* b = reinterpret_cast<float*>(&c[2]) + q;
+      *r = (*r * W[q] + s[q].x) / wn;
+      *g = (*g * W[q] + s[q].y) / wn;
+      *b = (*b * W[q] + s[q].z) / wn;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) *reinterpret_cast<float4*>(cp + k * kVoxPerBlock) = c[k];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) cs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Merge of a span of kSpanBlocks consecutive pool indices [p0, p0 + n) by a
 // 256-thread CTA: the span's touch epochs are read in one round (.cg), the
 // blocks holding the scan's epoch `ep` compacted into shared memory with a
 // warp ballot, then merged two per half CTA.  Returns this thread's merged
-// voxels; *touched (every thread) gets the span's touched blocks.
+// voxels; *touched (every thread) gets the span's touched blocks.  kColour:
+// the colour update of colour submaps is compiled in (kernels whose scans
+// include no colour scan, and so no colour submap, leave it out).
 constexpr int kSpanBlocks = 32;
 
 struct SpanList {
@@ -948,6 +1000,7 @@ struct SpanList {
   int n;
 };
 
+template <bool kColour = true>
 __device__ __forceinline__ int merge_span(const SubmapDev& m, int p0, int n, uint32_t ep, bool skip, SpanList* sl,
                                           int* touched) {
   const int tid = threadIdx.x;
@@ -963,6 +1016,15 @@ __device__ __forceinline__ int merge_span(const SubmapDev& m, int p0, int n, uin
   int merged = 0;
   for (int k = 2 * half; k < cnt; k += 4) {
     const int q = k + 1 < cnt ? sl->pool[k + 1] : -1;
+    if (kColour && m.C) {
+      if (m.storage == 0) {
+        merge_colour<0>(m, sl->pool[k], skip, sub);
+        if (q >= 0) merge_colour<0>(m, q, skip, sub);
+      } else {
+        merge_colour<1>(m, sl->pool[k], skip, sub);
+        if (q >= 0) merge_colour<1>(m, q, skip, sub);
+      }
+    }
     merged += m.storage == 0 ? merge_pools<0>(m, sl->pool[k], q, skip, sub) : merge_pools<1>(m, sl->pool[k], q, skip, sub);
   }
   *touched = cnt;

@@ -551,10 +551,15 @@ struct WeightParamsSmem {
   float w1[kH * kIn], b1[kH], w2[kH * kH], b2[kH], w3[kH], b3;
 };
 
-__global__ void __launch_bounds__(kFtW * kFtH) point_weights_kernel(const float* __restrict__ params,
-                                                                      const float* __restrict__ pts, int H, int W,
-                                                                      int sensor, float max_range,
-                                                                      float* __restrict__ wout) {
+// Features and network of n_frames organised scans [n_frames, H, W, 3] in one
+// persistent launch: CTAs take (frame, 32 x 8 tile) items in frame-major
+// order.  The weight fragments stay in registers across items; the biases and
+// output weights are read from shared memory (broadcast), which keeps three
+// 256-thread CTAs resident per SM.
+__global__ void __launch_bounds__(kFtW * kFtH, 3) point_weights_kernel(const float* __restrict__ params,
+                                                                         const float* __restrict__ pts, int n_frames,
+                                                                         int H, int W, int sensor, float max_range,
+                                                                         float* __restrict__ wout) {
   __shared__ FeatTile T;
   __shared__ WeightParamsSmem S;
   for (int q = threadIdx.x; q < kP; q += blockDim.x) {
@@ -571,7 +576,6 @@ __global__ void __launch_bounds__(kFtW * kFtH) point_weights_kernel(const float*
   // B fragments (col-major K x N, B[k][n] = W[n][k]) of both layers, and the
   // per-column biases / output weights this lane's accumulator columns see
   uint32_t B1[4], B2[4][2][2];
-  float b1c[4][2], b2c[4][2], w3c[4][2];
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
     const int n = nt * 8 + g;
@@ -583,22 +587,18 @@ __global__ void __launch_bounds__(kFtW * kFtH) point_weights_kernel(const float*
       B2[nt][kt][0] = pack_bf16(S.w2[n * kH + k], S.w2[n * kH + k + 1]);
       B2[nt][kt][1] = pack_bf16(S.w2[n * kH + k + 8], S.w2[n * kH + k + 9]);
     }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int col = nt * 8 + tig * 2 + j;
-      b1c[nt][j] = S.b1[col];
-      b2c[nt][j] = S.b2[col];
-      w3c[nt][j] = S.w3[col];
-    }
   }
-  const float b3 = S.b3;
   const int tiles_x = (W + kFtW - 1) / kFtW;
   const int n_tiles = tiles_x * ((H + kFtH - 1) / kFtH);
+  const long long n_items = (long long)n_tiles * n_frames;
   const int tx = threadIdx.x % kFtW, ty = threadIdx.x / kFtW;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int frame = (int)(item / n_tiles), tile = (int)(item % n_tiles);
+    const float* fpts = pts + (size_t)frame * H * W * 3;
+    float* fw = wout + (size_t)frame * H * W;
     const int x0 = (tile % tiles_x) * kFtW - kHalo, y0 = (tile / tiles_x) * kFtH - kHalo;
     __syncthreads();   // the previous tile's staging is no longer read
-    stage_tile(T, pts, H, W, sensor, x0, y0);
+    stage_tile(T, fpts, H, W, sensor, x0, y0);
     __syncthreads();
     const int u = x0 + kHalo + tx, v = y0 + kHalo + ty;
     float f[3] = {0.0f, 0.0f, 0.0f};
@@ -630,8 +630,9 @@ __global__ void __launch_bounds__(kFtW * kFtH) point_weights_kernel(const float*
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int nt = 2 * kt + h;
-          A2[kt][2 * h] = pack_bf16(fmaxf(C[nt][0] + b1c[nt][0], 0.0f), fmaxf(C[nt][1] + b1c[nt][1], 0.0f));
-          A2[kt][2 * h + 1] = pack_bf16(fmaxf(C[nt][2] + b1c[nt][0], 0.0f), fmaxf(C[nt][3] + b1c[nt][1], 0.0f));
+          const float c0 = S.b1[nt * 8 + tig * 2], c1 = S.b1[nt * 8 + tig * 2 + 1];
+          A2[kt][2 * h] = pack_bf16(fmaxf(C[nt][0] + c0, 0.0f), fmaxf(C[nt][1] + c1, 0.0f));
+          A2[kt][2 * h + 1] = pack_bf16(fmaxf(C[nt][2] + c0, 0.0f), fmaxf(C[nt][3] + c1, 0.0f));
         }
       }
       // the A layout wants {row g, cols k..k+1}, {row g+8, k..}, {row g, k+8..}, {row g+8, k+8..}
@@ -657,21 +658,23 @@ __global__ void __launch_bounds__(kFtW * kFtH) point_weights_kernel(const float*
       for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          oa += w3c[nt][j] * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][j] + b2c[nt][j], 0.0f)));
-          ob += w3c[nt][j] * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][2 + j] + b2c[nt][j], 0.0f)));
+          const int col = nt * 8 + tig * 2 + j;
+          const float b2 = S.b2[col], w3 = S.w3[col];
+          oa += w3 * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][j] + b2, 0.0f)));
+          ob += w3 * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][2 + j] + b2, 0.0f)));
         }
       oa += __shfl_xor_sync(0xffffffffu, oa, 1);
       oa += __shfl_xor_sync(0xffffffffu, oa, 2);
       ob += __shfl_xor_sync(0xffffffffu, ob, 1);
       ob += __shfl_xor_sync(0xffffffffu, ob, 2);
-      wpt[mt] = tig == 0 ? softplus_f(oa + b3) : (tig == 1 ? softplus_f(ob + b3) : 0.0f);
+      wpt[mt] = tig == 0 ? softplus_f(oa + S.b3) : (tig == 1 ? softplus_f(ob + S.b3) : 0.0f);
     }
     // lane (g, tig) holds the weights of points mt*16 + g (tig 0) and + 8 (tig 1)
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
       const int pt = mt * 16 + g + (tig == 1 ? 8 : 0);
       const int gu = x0 + kHalo + pt;
-      if (tig < 2 && gu < W && v < H) wout[(size_t)v * W + gu] = wpt[mt];
+      if (tig < 2 && gu < W && v < H) fw[(size_t)v * W + gu] = wpt[mt];
     }
   }
 }
@@ -838,17 +841,25 @@ cvx_status cvx_weight_model_infer(cvx_weight_model* w, const float* features, in
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
 
-cvx_status cvx_weight_model_point_weights(cvx_weight_model* w, const float* points, int32_t height, int32_t width,
-                                          int32_t sensor, float max_range, float* weights, void* stream) {
-  if (!w || !points || !weights || height <= 0 || width <= 0 || (sensor != 0 && sensor != 1) || !(max_range > 0))
+cvx_status cvx_weight_model_point_weights_frames(cvx_weight_model* w, const float* points, int32_t n_frames,
+                                                 int32_t height, int32_t width, int32_t sensor, float max_range,
+                                                 float* weights, void* stream) {
+  if (!w || !points || !weights || n_frames <= 0 || height <= 0 || width <= 0 || (sensor != 0 && sensor != 1) ||
+      !(max_range > 0))
     return CVX_ERR_INVALID_ARG;
+  if ((long long)n_frames * height * width > (1ll << 40)) return CVX_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  const int tiles = ((width + kFtW - 1) / kFtW) * ((height + kFtH - 1) / kFtH);
-  const int grid = std::min(tiles, num_sms() * 4);
-  COVOX_LAUNCH(kKMlpFwd, s,
-               point_weights_kernel<<<grid, kFtW * kFtH, 0, s>>>(w->params, points, height, width, sensor,
+  const long long items = (long long)((width + kFtW - 1) / kFtW) * ((height + kFtH - 1) / kFtH) * n_frames;
+  const int grid = (int)std::min<long long>(items, (long long)num_sms() * 3);
+  COVOX_LAUNCH(kKPointWeights, s,
+               point_weights_kernel<<<grid, kFtW * kFtH, 0, s>>>(w->params, points, n_frames, height, width, sensor,
                                                                   max_range, weights));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
+}
+
+cvx_status cvx_weight_model_point_weights(cvx_weight_model* w, const float* points, int32_t height, int32_t width,
+                                          int32_t sensor, float max_range, float* weights, void* stream) {
+  return cvx_weight_model_point_weights_frames(w, points, 1, height, width, sensor, max_range, weights, stream);
 }
 
 cvx_status cvx_weight_model_train_step(cvx_weight_model* w, const float* features, const float* e2,
@@ -910,7 +921,7 @@ cvx_status cvx_training_targets(cvx_submap* clean, const float* points, int64_t 
   if (!clean || clean->p.storage != CVX_STORE_F32 || !e2 || !mask) return CVX_ERR_INVALID_ARG;
   ScanDev sc;
   int lb = 0;
-  const cvx_status v = make_scan_dev(clean, points, n, T, nullptr, ip, &sc, &lb);
+  const cvx_status v = make_scan_dev(clean, points, n, T, nullptr, ip, &sc, &lb, nullptr, false);
   if (v != CVX_OK) return v;
   if (n == 0) return CVX_OK;
   cudaStream_t s = (cudaStream_t)stream;

@@ -14,7 +14,7 @@ const char* kNames[covox::kNumKinds] = {"alloc_kernel",    "integrate_kernel", "
                                         "mlp_fwd_kernel",  "mlp_bwd_kernel", "adam_kernel",
                                         "targets_kernel", "integrate_pipelined_kernel", "flush_kernel",
                                         "pipe_close_kernel", "esdf_kernels",
-                                        "hash_kernels", "discard_sums_kernel"};
+                                        "hash_kernels", "discard_sums_kernel", "point_weights_kernel"};
 
 struct Rec {
   int kind;

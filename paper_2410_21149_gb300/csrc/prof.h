@@ -24,7 +24,8 @@ enum KernelKind : int {
   kKEsdf = 13,      // distance field of a submap
   kKHash = 14,      // stand-alone block hash insert / find
   kKDiscard = 15,   // reset: per-scan sums a launch left unmerged
-  kNumKinds = 16
+  kKPointWeights = 16,   // fused features + weight network of organised scans
+  kNumKinds = 17
 };
 
 void prof_begin(int kind, cudaStream_t s);

@@ -17,6 +17,7 @@ struct cvx_submap {
   covox::SubmapDev dev_b;   // the second per-scan set of a pipelined submap
   covox::SubmapDev dev_cd[2];   // the third and fourth per-scan sets of a four-set submap
   int n_sets;               // per-scan sets: 1, 2 (pipelined) or 4
+  bool colour;              // CVX_SUBMAP_COLOR: fused RGB planes and per-set colour sums
   bool pipelined;
   bool maybe_pending;       // a pipelined per-scan launch may have left a scan unmerged
   size_t bytes_per_vox;
@@ -24,7 +25,7 @@ struct cvx_submap {
   struct Alloc {
     void* ptr;
     size_t bytes;
-  } allocs[24];
+  } allocs[32];
   int n_allocs;
 };
 
@@ -55,10 +56,16 @@ constexpr int kMaxLocalBlocks = 16;   // 8 KB of fixed-point sums each
 
 // Validate one scan's arguments and fill its device descriptor (with the
 // tile layout).  Returns CVX_OK or CVX_ERR_INVALID_ARG; *lb gets the number
-// of shared-memory block slots per CTA.
+// of shared-memory block slots per CTA.  rgb: per-point colours, required
+// (n > 0) when integrating into a colour submap and refused by any other;
+// colour scans accumulate in the L2 mode (*lb = 0).  integrating = false
+// (a scan that is only read against the submap) lifts the requirement.
 inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t n, const float* T,
-                                const float* pw, const cvx_integrate_params* ip, ScanDev* sc, int* lb) {
+                                const float* pw, const cvx_integrate_params* ip, ScanDev* sc, int* lb,
+                                const float* rgb = nullptr, bool integrating = true) {
   if (!map || !ip || !T || n < 0 || (n > 0 && !pts)) return CVX_ERR_INVALID_ARG;
+  if (rgb && (!map->colour || !integrating)) return CVX_ERR_INVALID_ARG;
+  if (map->colour && integrating && n > 0 && !rgb) return CVX_ERR_INVALID_ARG;
   for (int q = 0; q < 12; ++q)
     if (!std::isfinite(T[q])) return CVX_ERR_INVALID_ARG;
   if (ip->weight_mode < 0 || ip->weight_mode > 2 || ip->dropoff < 0 || ip->dropoff > 2)
@@ -77,6 +84,7 @@ inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t
   std::memset(sc, 0, sizeof(*sc));
   sc->pts = pts;
   sc->pw = pw;
+  sc->rgb = rgb;
   sc->n = n;
   std::memcpy(sc->T, T, sizeof(sc->T));
   sc->min_range = ip->min_range;
@@ -106,7 +114,12 @@ inline cvx_status make_scan_dev(const cvx_submap* map, const float* pts, int64_t
     sc->n_tiles = (int)((n + run - 1) / run);
   }
   *lb = ip->local_blocks > 0 ? ip->local_blocks : (ip->local_blocks < 0 ? 0 : kDefaultLocalBlocks);
+  if (rgb) *lb = 0;
   return CVX_OK;
 }
+
+// A scan the compile-time variants do not cover: carving, bands longer than
+// 512 cells per axis, colours (the run-time dispatching kernel runs it).
+inline int general_form(const ScanDev& sc) { return sc.carve || sc.long_band || sc.rgb != nullptr; }
 
 }  // namespace covox

@@ -143,6 +143,18 @@ def learned_point_weights(model: WeightModel, scan_points, height: int, width: i
     return w
 
 
+def learned_point_weights_frames(model: WeightModel, frames_points, height: int, width: int, sensor: int,
+                                 max_range: float, out=None, stream=None):
+    """Per-point weights of n organised scans of one shape in one launch:
+    frames_points CUDA float32 [n, height*width, 3]; returns [n, height*width]."""
+    import torch
+    n = int(frames_points.shape[0])
+    w = torch.empty((n, height * width), dtype=torch.float32, device=frames_points.device) if out is None else out
+    _capi.cvx_weight_model_point_weights_frames(model.handle, frames_points, n, height, width, sensor, max_range,
+                                                w, stream)
+    return w
+
+
 def gate(rmse_learned: float, rmse_plain: float) -> bool:
     """Keep the learned weight only where it lowers the SDF RMSE against the
     scene (measured by the caller on validation data); otherwise the plain

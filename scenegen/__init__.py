@@ -525,3 +525,20 @@ WORKLOADS = {
     "c3": make_c3,
     "c4": make_c4,
 }
+
+
+def point_colors(scan: Scan, seed: int = 0, period: float = 1.5) -> np.ndarray:
+    """float32 [N, 3] colours in [0, 1] of a scan's points: a seeded procedural
+    albedo of the point's submap-frame position (one sinusoid per channel,
+    direction and phase drawn from `seed`, spatial period `period` metres), so
+    scans that see the same surface agree up to their range noise.  Points
+    without a return get colour 0."""
+    rng = np.random.default_rng(10_000 + seed)
+    dirs = rng.normal(size=(3, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    phase = rng.uniform(0, 2 * np.pi, 3)
+    T = np.asarray(scan.T_sub_sensor, np.float64).reshape(3, 4)
+    p = scan.points.astype(np.float64) @ T[:, :3].T + T[:, 3]
+    c = 0.5 + 0.5 * np.sin(p @ dirs.T * (2 * np.pi / period) + phase)
+    c[~np.isfinite(c).all(axis=1)] = 0.0
+    return np.ascontiguousarray(c, dtype=np.float32)

@@ -248,3 +248,21 @@ def test_fused_point_weights_match_features_then_inference():
         rel_o = np.abs(fused / w_orc - 1)[valid]
         assert np.quantile(rel_o, 0.999) < 1e-2, np.quantile(rel_o, 0.999)
     m.close()
+
+
+def test_point_weights_of_many_frames_in_one_launch():
+    """cvx_weight_model_point_weights_frames over five scans (one persistent
+    launch over (frame, tile) items) equals the single-scan entry point on
+    each scan, bit for bit: the same arithmetic per point."""
+    import torch
+    from paper_2410_21149_gb300 import weights
+    m = weights.WeightModel(omlp.flatten(_rand_params(5)).astype(np.float32))
+    wl = sg.make_c2(seed=23, n_frames=5, width=320, height=238)
+    scans = wl.submaps[0].scans
+    H, W = scans[0].height, scans[0].width
+    pts = torch.from_numpy(np.stack([sc.points for sc in scans])).cuda()
+    many = weights.learned_point_weights_frames(m, pts, H, W, 0, 10.0).cpu().numpy()
+    for f in range(len(scans)):
+        one = weights.learned_point_weights(m, pts[f], H, W, 0, 10.0).cpu().numpy()
+        assert np.array_equal(many[f], one), f
+    m.close()

@@ -90,3 +90,28 @@ def test_colour_is_linear_per_channel():
     _, _, _, C2 = _run(scans, poses, [(0.5 * c + 0.25).astype(np.float32) for c in cols])
     m = np.broadcast_to((W > 0)[:, None, :], C.shape)
     assert np.abs(C2[m] - (0.5 * C[m] + 0.25)).max() < 1e-12
+
+
+def test_non_finite_colour_drops_its_point():
+    """A point with a NaN or infinite colour channel is skipped: the run equals
+    the run without those points, in D, W, C and the valid-point count."""
+    scans, poses = _scans()
+    rng = np.random.default_rng(5)
+    cols = [rng.uniform(0, 1, (len(s), 3)).astype(np.float32) for s in scans]
+    bad = []
+    for c in cols:
+        b = rng.choice(len(c), len(c) // 10, replace=False)
+        c[b[0::3], 0] = np.nan
+        c[b[1::3], 1] = np.inf
+        c[b[2::3], 2] = -np.inf
+        bad.append(b)
+    m1 = orc.OracleSubmap(0.1, 0.3, 1e4)
+    m2 = orc.OracleSubmap(0.1, 0.3, 1e4)
+    v1 = v2 = 0
+    for s, T, c, b in zip(scans, poses, cols, bad):
+        v1 += m1.integrate(s, T, None, 1, 1, 0.1, 20.0, 0, colors=c)["valid"]
+        keep = np.setdiff1d(np.arange(len(s)), b)
+        v2 += m2.integrate(s[keep], T, None, 1, 1, 0.1, 20.0, 0, colors=c[keep])["valid"]
+    assert v1 == v2 and v1 > 0
+    for a, b in zip(m1.extract() + (m1.extract_colors(),), m2.extract() + (m2.extract_colors(),)):
+        assert np.array_equal(a, b)
