@@ -237,8 +237,7 @@ def bench_multi(wl, storage, steps, warmup, ws, max_blocks=1 << 16, sequential=T
                                     sc.height, sc.width, ppc, lb)
 
     def reset(st=None):
-        for s in subs:
-            s.reset(st)
+        _capi.cvx_reset_submaps(handles, st)
 
     tuned = autotune.tune_batch(handles, [(m, p, T, None, prm(sc)) for m, p, T, sc in items],
                                 f"{wl.name}|st{storage}|p{int(pipelined)}|s{sets}", reset=reset, force=tune_force)
@@ -525,7 +524,7 @@ def run_ours(args):
     bytes_kernel = {
         # the whole frame sequence: points, hash probes and new keys, D/W of the merged voxels
         "batched_kernel": 12 * F * N + 16 * blocks + 12 * new_blocks + 2 * S32 * merged,
-        "zero_pool_kernel": S32 * 512 * new_blocks,
+        "reset_pools_kernel": S32 * 512 * new_blocks,
     }
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     dom_ms = prof[dom][0] / prof[dom][1]

@@ -194,6 +194,13 @@ cvx_status cvx_extract_blocks(cvx_submap* map, int64_t capacity, int32_t* keys, 
  * per-scan sums a launch that gave up (CVX_ERR_TIMEOUT) left unmerged. */
 cvx_status cvx_reset_submap(cvx_submap* map, void* stream);
 
+/* cvx_reset_submap() of n distinct submaps (asynchronous): two kernel
+ * launches per 48 submaps instead of a handful of launches and copies per
+ * submap, for mappers that keep many submaps (one per stretch of the
+ * trajectory, Sec. III-C) and clear them together.  INVALID_ARG if maps is NULL (n > 0) or holds a
+ * NULL entry; nothing is launched then. */
+cvx_status cvx_reset_submaps(cvx_submap* const* maps, int32_t n, void* stream);
+
 /* Pipelined submap: merge the scan the last cvx_integrate_scan() left
  * pending, asynchronously on `stream` (one kernel; nothing when no scan is
  * pending on the device).  Other submaps: no-op.  Coalescing the per-scan
@@ -436,9 +443,9 @@ cvx_status cvx_normalise_targets(float* e2, const float* mask, int64_t n, float*
  * and results as cvx_integrate_scan() on float32 storage, into submap storage
  * the caller owns and describes with a cvx_submap_view.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.  Its per-scan scratch
- * (per-voxel sums and the blocks' touch epochs, about 16 MiB) is one fixed array
- * in device memory that every GPU loading this library holds until the
- * process exits.
+ * (per-voxel sums, the blocks' touch epochs and their voxel groups' touch
+ * tags, about 16.5 MiB) is one fixed array in device memory that every GPU
+ * loading this library holds until the process exits.
  *   - The first call on a device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress) and sets a kernel
  *     attribute; make that first call before any stream capture.

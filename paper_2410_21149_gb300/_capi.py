@@ -95,6 +95,7 @@ SIGNATURES = {
     "cvx_extract_blocks": (_i32, [_vp, _i64, _vp, _vp, _vp, ctypes.POINTER(_i64), _vp]),
     "cvx_extract_colors": (_i32, [_vp, _i64, _vp, ctypes.POINTER(_i64), _vp]),
     "cvx_reset_submap": (_i32, [_vp, _vp]),
+    "cvx_reset_submaps": (_i32, [ctypes.POINTER(_vp), _i32, _vp]),
     "cvx_submap_status": (_i32, [_vp]),
     "cvx_flush_submap": (_i32, [_vp, _vp]),
     "cvx_registration_points": (_i32, [_vp, ctypes.c_float, ctypes.c_float, _i64, _vp, _vp, _vp]),
@@ -293,6 +294,11 @@ def cvx_extract_blocks(handle: int, capacity: int, keys, dist, weight, stream=No
 
 def cvx_reset_submap(handle: int, stream=None) -> None:
     check(lib().cvx_reset_submap(handle, _stream_handle(stream)), "cvx_reset_submap")
+
+
+def cvx_reset_submaps(handles, stream=None) -> None:
+    arr = (_vp * max(len(handles), 1))(*handles)
+    check(lib().cvx_reset_submaps(arr, len(handles), _stream_handle(stream)), "cvx_reset_submaps")
 
 
 def cvx_compute_esdf(handle: int, site_band: float, w_min: float, max_dist: float, out, sq_dist=None,

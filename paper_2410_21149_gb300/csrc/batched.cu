@@ -62,7 +62,7 @@ struct BatchDev {
   const int* seg_code;      // [n_segs] scan index, bit 30 set for a merge segment
   int n_segs;
   int n_scans;
-  int* ctr;                 // head, err, exit count, spare, then per scan: tiles done, merge tickets, merged flag
+  int* ctr;                 // head, err, exit count, scans closed, then per scan: tiles done, merge tickets, merged flag
   unsigned long long* phase_ns;   // [1 + 2 * n_scans]: launch start, per scan tiles done / merged
   long long polls;          // polls before a wait gives up
   int missing_cta;          // test hook: this CTA takes one item and leaves without doing it (-1: none)
@@ -124,15 +124,15 @@ __device__ __forceinline__ unsigned long long cta_sum_b(unsigned long long v, un
 // submap's allocated blocks (blocks the submap's next scan allocates
 // meanwhile carry other epochs, so any count read now covers this scan's).
 template <bool kColour>
-__device__ void merge_part(const BatchDev& b, int s, int part, SpanList* sl, unsigned long long* red) {
+__device__ void merge_part(const BatchDev& b, int s, int part, const MergeSmem& ms, unsigned long long* red) {
   const SubmapDev& m = b.views[b.meta[s].view];
   const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
   const bool skip = *((volatile int32_t*)m.frame_err) != 0;
   const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u + b.scans[s].epoch_add;
   unsigned long long merged = 0, touched = 0;
-  for (int span = part; span * kSpanBlocks < nb; span += kMergeParts) {
+  for (int span = part; span * kSpanBlocks < nb; span += kSpansPerCall * kMergeParts) {
     int t = 0;
-    merged += merge_span<kColour>(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl, &t);
+    merged += merge_span<kColour>(m, span, kMergeParts, nb, ep, skip, ms, &t);
     touched += t;
   }
   const unsigned long long c = cta_sum_b(merged, red);
@@ -151,6 +151,7 @@ __device__ void close_scan(const BatchDev& b, int s) {
   st->sticky_err |= *((volatile int32_t*)m.frame_err);
   *m.frame_err = 0;
   if (sm.epoch_end > 0) st->epoch += (uint32_t)sm.epoch_end;   // after the submap's last scan of the launch
+  atomicAdd(b.ctr + 3, 1);
 }
 
 // The queue segment holding item it (read-only descriptors: through the
@@ -169,7 +170,6 @@ __global__ void __launch_bounds__(kTileThreads, 3) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int item_smem[3];
   __shared__ int ok_smem;
-  __shared__ SpanList span;
   __shared__ unsigned long long red[kTileThreads / 32];
   if (b.phase_ns && blockIdx.x == 0 && threadIdx.x == 0) b.phase_ns[0] = global_ns();
   const int n_items = __ldg(b.seg_first + b.n_segs);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) batched_kernel(BatchDev b) {
         if (!wait_at_least(b, merged_flag(b, sm.prev), 1, &ok_smem)) continue;
         seen_merged = sm.prev;
       }
-      merge_part<(kVariant < 0)>(b, s, part, &span, red);
+      merge_part<(kVariant < 0)>(b, s, part, merge_smem(smem), red);
       if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(merge_ticket(b, s), 1) == kMergeParts - 1) {
@@ -222,16 +222,12 @@ __global__ void __launch_bounds__(kTileThreads, 3) batched_kernel(BatchDev b) {
       __syncthreads();
     }
   }
-  // the last CTA to leave checks that every scan was merged
+  // the last CTA to leave checks that every scan was merged (each CTA
+  // fenced its closes before counting itself out)
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(b.ctr + 2, 1) == gridDim.x - 1) {
-      for (int s = 0; s < b.n_scans; ++s)
-        if (*((volatile int*)merged_flag(b, s)) == 0) {
-          atomicOr(b.ctr + 1, kErrIncomplete);
-          break;
-        }
-    }
+    if (atomicAdd(b.ctr + 2, 1) == gridDim.x - 1 && *((volatile int*)(b.ctr + 3)) != b.n_scans)
+      atomicOr(b.ctr + 1, kErrIncomplete);
   }
 }
 

@@ -11,6 +11,7 @@ namespace covox {
 
 constexpr int kVoxPerBlock = 512;           // 8^3
 constexpr uint64_t kEmptyKey = ~0ull;       // unreachable: packed keys use 63 bits
+constexpr int kGroupsPerBlock = kVoxPerBlock / 4;   // 4-voxel groups: local index >> 2
 constexpr float kKeyLimit = 8388608.0f;     // 2^23 voxels = 2^20 blocks per axis
 
 enum : int32_t { kErrCapacity = 1, kErrKeyRange = 2, kErrTimeout = 4 };
@@ -42,6 +43,9 @@ struct SubmapDev {
   float2* acc;                // [max_blocks,512] per-scan sums (sum w (d - trunc), sum w), zero between scans
   uint32_t* tepoch;           // [max_blocks] epoch of the last scan of this per-scan set that touched the
                               // block: the scan's touched blocks are those holding its epoch
+  uint8_t* gep;               // [max_blocks,128] touch tag of each 4-voxel group (a run of 4 along x) by
+                              // this per-scan set: group_tag() of the last scan that observed a voxel of
+                              // it, so a merge reads the sums of touched groups only
   float4* cacc;               // colour submaps: [max_blocks,512] per-scan colour sums (sum w r, sum w g,
                               // sum w b, 0) of this set, zero between scans; nullptr otherwise
   float* C;                   // colour submaps: [max_blocks,3,512] fused RGB planes; nullptr otherwise

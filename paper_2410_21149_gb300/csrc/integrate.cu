@@ -69,7 +69,7 @@ __device__ __forceinline__ unsigned long long cta_sum(unsigned long long v, unsi
 // closes the frame at once; the others merge from the values they read.
 __global__ void __launch_bounds__(kTileThreads) merge_kernel(SubmapDev m) {
   __shared__ int head[3];
-  __shared__ SpanList sl;
+  __shared__ MergeSmemStatic sl;
   __shared__ unsigned long long red[kTileThreads / 32];
   if (threadIdx.x == 0) {
     const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
@@ -93,9 +93,9 @@ __global__ void __launch_bounds__(kTileThreads) merge_kernel(SubmapDev m) {
   const bool skip = head[1] != 0;
   const uint32_t ep = (uint32_t)head[2];
   unsigned long long merged = 0, touched = 0;
-  for (int p0 = blockIdx.x * kSpanBlocks; p0 < nb; p0 += gridDim.x * kSpanBlocks) {
+  for (int span = blockIdx.x; span * kSpanBlocks < nb; span += kSpansPerCall * gridDim.x) {
     int t = 0;
-    merged += merge_span(m, p0, min(kSpanBlocks, nb - p0), ep, skip, &sl, &t);
+    merged += merge_span(m, span, gridDim.x, nb, ep, skip, sl.view(), &t);
     touched += t;
   }
   const unsigned long long sum = cta_sum(merged, red);
@@ -105,58 +105,96 @@ __global__ void __launch_bounds__(kTileThreads) merge_kernel(SubmapDev m) {
   }
 }
 
-// Clear the per-scan sums a launch that gave up left unmerged: the blocks of
-// either per-scan set stamped with an epoch after the last closed one (a
-// batched launch numbers its scans st->epoch + 1, + 2, ... and closes them
-// all at its end; a pending pipelined scan was dropped before this runs).
-// Reset only: merged blocks hold zero sums, so this at most repeats zeroing.
-struct SetViews {
-  SubmapDev v[4];
+// Reset of up to kResetMaps submaps in two launches.  reset_pools_kernel:
+// every hash slot emptied, the pool planes (D, W, colours) of the allocated
+// blocks zeroed, every touch epoch and group tag cleared, and the per-scan sums a launch
+// that gave up left unmerged cleared too: the blocks of a per-scan set
+// stamped with an epoch after the last closed one (a batched launch numbers
+// its scans st->epoch + 1, + 2, ... and closes them all at its end; a pending
+// pipelined scan was dropped before this runs; merged blocks hold zero sums).
+// Only blocks below min(n_blocks, max_blocks) ever receive an epoch.  The
+// submaps' State words are read here and zeroed by reset_states_kernel
+// afterwards.
+constexpr int kResetMaps = 48;
+
+struct ResetDesc {
+  unsigned long long* keys;
+  int32_t* vals;
+  State* st;
+  uint4 *D, *W, *C;              // pool planes; C: colour submaps, else nullptr
+  float4* acc[4];                // per-scan sums of each set (float2 pairs)
+  float4* cacc[4];               // per-scan colour sums of each set, or nullptr
+  uint32_t* tepoch[4];
+  uint32_t* gep[4];              // group tags of each set (32-bit words)
+  long long slots;
+  int32_t max_blocks, n_sets;
+  int32_t plane16;               // 16-byte words of one block's D (or W) plane
 };
 
-__global__ void discard_sums_kernel(SetViews sets, int n_sets) {
-  const SubmapDev& a = sets.v[0];
-  const int nb = min(a.st->n_blocks, a.max_blocks);
-  const uint32_t e = a.st->epoch;
-  for (int set = 0; set < n_sets; ++set) {
-    const SubmapDev& m = sets.v[set];
-    for (int p = blockIdx.x; p < nb; p += gridDim.x) {
-      const uint32_t t = m.tepoch[p];
+struct ResetBatch {
+  ResetDesc m[kResetMaps];
+  int32_t n;
+};
+
+__global__ void __launch_bounds__(256) reset_pools_kernel(const __grid_constant__ ResetBatch rb) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (int k = 0; k < rb.n; ++k) {
+    const ResetDesc& d = rb.m[k];
+    const int nb = min(d.st->n_blocks, d.max_blocks);
+    const uint32_t e = d.st->epoch;
+    for (long long q = tid; q < d.slots; q += nthr) {
+      d.keys[q] = kEmptyKey;
+      d.vals[q] = -1;
+    }
+    const long long n16 = (long long)nb * d.plane16;
+    for (long long q = tid; q < n16; q += nthr) {
+      d.D[q] = z;
+      d.W[q] = z;
+    }
+    if (d.C)
+      for (long long q = tid; q < 3 * (long long)nb * kVoxPerBlock / 4; q += nthr) d.C[q] = z;
+    // one warp per (set, block): lane 0 reads and clears the epoch
+    for (long long r = tid >> 5; r < (long long)d.n_sets * nb; r += nthr >> 5) {
+      const int set = (int)(r / nb), p = (int)(r % nb);
+      uint32_t t = 0;
+      if (lane == 0) {
+        t = d.tepoch[set][p];
+        if (t) d.tepoch[set][p] = 0u;
+      }
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (t == 0) continue;   // never touched by this set: its tags are clear
+      d.gep[set][(size_t)p * (kGroupsPerBlock / 4) + lane] = 0u;
       if (t <= e) continue;
-      float4* acc = reinterpret_cast<float4*>(m.acc + (size_t)p * kVoxPerBlock);
-      for (int q = threadIdx.x; q < kVoxPerBlock / 2; q += blockDim.x) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (m.cacc)
-        for (int q = threadIdx.x; q < kVoxPerBlock; q += blockDim.x)
-          m.cacc[(size_t)p * kVoxPerBlock + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4* a = d.acc[set] + (size_t)p * (kVoxPerBlock / 2);
+      for (int q = lane; q < kVoxPerBlock / 2; q += 32) a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (d.cacc[set]) {
+        float4* c = d.cacc[set] + (size_t)p * kVoxPerBlock;
+        for (int q = lane; q < kVoxPerBlock; q += 32) c[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
   }
 }
 
-// Zero the allocated part of the pool (reset), colour planes included.
-__global__ void zero_pool_kernel(SubmapDev m, int bytes_per_block) {
-  const long long nb = min(m.st->n_blocks, m.max_blocks);
-  const long long n16 = nb * bytes_per_block / 16;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n16; q += stride) {
-    reinterpret_cast<uint4*>(m.D)[q] = make_uint4(0, 0, 0, 0);
-    reinterpret_cast<uint4*>(m.W)[q] = make_uint4(0, 0, 0, 0);
-  }
-  if (m.C) {
-    const long long c16 = nb * 3 * kVoxPerBlock * 4 / 16;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < c16; q += stride)
-      reinterpret_cast<uint4*>(m.C)[q] = make_uint4(0, 0, 0, 0);
-  }
+__global__ void reset_states_kernel(const __grid_constant__ ResetBatch rb) {
+  constexpr int kWords = (int)(sizeof(State) / 4);
+  static_assert(sizeof(State) % 4 == 0, "State is a whole number of 32-bit words");
+  for (int q = threadIdx.x; q < rb.n * kWords; q += blockDim.x)
+    reinterpret_cast<uint32_t*>(rb.m[q / kWords].st)[q % kWords] = 0u;
 }
 
 // The per-scan set `which` of a pipelined submap: a describes set 0 (and
 // everything the sets share), b the second set (a copy of a but for acc,
-// tepoch and frame_err).
+// cacc, tepoch, gep and frame_err).
 __device__ __forceinline__ SubmapDev pick_set(const SubmapDev& a, const SubmapDev& b, int which) {
   SubmapDev m = a;
   if (which) {
     m.acc = b.acc;
     m.cacc = b.cacc;
     m.tepoch = b.tepoch;
+    m.gep = b.gep;
     m.frame_err = b.frame_err;
   }
   return m;
@@ -167,12 +205,11 @@ __device__ __forceinline__ SubmapDev pick_set(const SubmapDev& a, const SubmapDe
 // voxels and touched blocks to the submap's counters.
 template <bool kColour = true>
 __device__ __noinline__ void merge_set(const SubmapDev& m, int nb, uint32_t ep, bool skip, int first, int step,
-                                       SpanList* sl, unsigned long long* red) {
+                                       const MergeSmem& ms, unsigned long long* red) {
   unsigned long long merged = 0, touched = 0;
-  for (int span = first; span * kSpanBlocks < nb; span += step) {
+  for (int span = first; span * kSpanBlocks < nb; span += kSpansPerCall * step) {
     int t = 0;
-    merged += merge_span<kColour>(m, span * kSpanBlocks, min(kSpanBlocks, nb - span * kSpanBlocks), ep, skip, sl,
-                                  &t);
+    merged += merge_span<kColour>(m, span, step, nb, ep, skip, ms, &t);
     touched += t;
   }
   const unsigned long long sum = cta_sum(merged, red);
@@ -237,7 +274,6 @@ __global__ void __launch_bounds__(kTileThreads, 5) integrate_pipelined_kernel(Su
                                                                            int lb, int n_merge) {
   extern __shared__ __align__(16) char smem[];
   __shared__ unsigned long long red[kTileThreads / 32];
-  __shared__ SpanList sl;
   const int par = *((volatile int32_t*)&a.st->parity);
   if ((int)blockIdx.x < sc.n_tiles) {
     integrate_tile_v<kVariant>(pick_set(a, b, par), sc, (int)blockIdx.x, smem, lb);
@@ -249,7 +285,7 @@ __global__ void __launch_bounds__(kTileThreads, 5) integrate_pipelined_kernel(Su
   const int nb = min(*((volatile int32_t*)&a.st->n_blocks), a.max_blocks);
   const bool skip = *((volatile int32_t*)prev.frame_err) != 0;
   const uint32_t ep = *((volatile uint32_t*)&a.st->epoch);   // the previous scan's epoch
-  merge_set<(kVariant < 0)>(prev, nb, ep, skip, (int)blockIdx.x - sc.n_tiles, n_merge, &sl, red);
+  merge_set<(kVariant < 0)>(prev, nb, ep, skip, (int)blockIdx.x - sc.n_tiles, n_merge, merge_smem(smem), red);
 }
 
 // One thread, after integrate_pipelined_kernel: close the frame it merged
@@ -280,10 +316,10 @@ const PipelinedFn kPipelined[7] = {integrate_pipelined_kernel<-1>, integrate_pip
 __global__ void __launch_bounds__(kTileThreads) flush_kernel(SubmapDev a, SubmapDev b, int discard) {
   __shared__ PipeHead h;
   __shared__ unsigned long long red[kTileThreads / 32];
-  __shared__ SpanList sl;
+  __shared__ MergeSmemStatic sl;
   pipe_head(a, b, 0, false, &h);
   if (!h.pending) return;   // uniform over the grid
-  merge_set(pick_set(a, b, h.par ^ 1), h.nb, h.ep, discard || h.fe != 0, blockIdx.x, gridDim.x, &sl, red);
+  merge_set(pick_set(a, b, h.par ^ 1), h.nb, h.ep, discard || h.fe != 0, blockIdx.x, gridDim.x, sl.view(), red);
 }
 
 }  // namespace
@@ -392,17 +428,20 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   d.W = sub_alloc(m, nb * kVoxPerBlock * m->bytes_per_vox);
   d.acc = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
   d.tepoch = (uint32_t*)sub_alloc(m, nb * 4);
+  d.gep = (uint8_t*)sub_alloc(m, nb * kGroupsPerBlock);
   d.st = (State*)sub_alloc(m, sizeof(State));
   m->n_sets = (p->flags & CVX_SUBMAP_FOUR_SETS) ? 4 : ((p->flags & CVX_SUBMAP_PIPELINED) ? 2 : 1);
   m->pipelined = m->n_sets > 1;
   m->colour = (p->flags & CVX_SUBMAP_COLOR) != 0;
-  const int expect = 8 + 2 * (m->n_sets - 1) + (m->colour ? 1 + m->n_sets : 0);
+  const int expect = 9 + 3 * (m->n_sets - 1) + (m->colour ? 1 + m->n_sets : 0);
   float2* acc_x[3] = {nullptr, nullptr, nullptr};
   uint32_t* tep_x[3] = {nullptr, nullptr, nullptr};
+  uint8_t* gep_x[3] = {nullptr, nullptr, nullptr};
   float4* cacc_x[4] = {nullptr, nullptr, nullptr, nullptr};
-  for (int k = 1; k < m->n_sets; ++k) {   // further per-scan sets: sums and touch epochs
+  for (int k = 1; k < m->n_sets; ++k) {   // further per-scan sets: sums, touch epochs and group tags
     acc_x[k - 1] = (float2*)sub_alloc(m, nb * kVoxPerBlock * sizeof(float2));
     tep_x[k - 1] = (uint32_t*)sub_alloc(m, nb * 4);
+    gep_x[k - 1] = (uint8_t*)sub_alloc(m, nb * kGroupsPerBlock);
   }
   if (m->colour) {   // RGB planes, and colour sums per per-scan set
     d.C = (float*)sub_alloc(m, nb * 3 * kVoxPerBlock * sizeof(float));
@@ -430,6 +469,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
     v.acc = acc_x[k - 1];
     v.cacc = cacc_x[k];
     v.tepoch = tep_x[k - 1];
+    v.gep = gep_x[k - 1];
     v.frame_err = fe_x[k - 1];
   }
   cudaStream_t s = (cudaStream_t)p->stream;
@@ -437,6 +477,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   cudaMemsetAsync(d.keys, 0xff, slots * 8, s);
   cudaMemsetAsync(d.vals, 0xff, slots * 4, s);
   cudaMemsetAsync(d.tepoch, 0, nb * 4, s);
+  cudaMemsetAsync(d.gep, 0, nb * kGroupsPerBlock, s);
   cudaMemsetAsync(d.D, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.W, 0, nb * kVoxPerBlock * m->bytes_per_vox, s);
   cudaMemsetAsync(d.acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
@@ -444,6 +485,7 @@ cvx_status cvx_create_submap(const cvx_submap_params* p, cvx_submap** out) {
   for (int k = 1; k < m->n_sets; ++k) {
     cudaMemsetAsync(set_view(m, k).acc, 0, nb * kVoxPerBlock * sizeof(float2), s);
     cudaMemsetAsync(set_view(m, k).tepoch, 0, nb * 4, s);
+    cudaMemsetAsync(set_view(m, k).gep, 0, nb * kGroupsPerBlock, s);
   }
   if (m->colour) {
     cudaMemsetAsync(d.C, 0, nb * 3 * kVoxPerBlock * sizeof(float), s);
@@ -485,7 +527,7 @@ cvx_status integrate_scan(cvx_submap* map, const float* points_xyz, int64_t n, c
   }
   const IntegrateFn fn = kIntegrate[tile_variant(lb, sc.dropoff, general_form(sc)) + 1];
   COVOX_LAUNCH(kKAccum, s, fn<<<sc.n_tiles, kTileThreads, smem, s>>>(map->dev, sc, lb));
-  const int grid = std::min<int>((map->dev.max_blocks + kSpanBlocks - 1) / kSpanBlocks, num_sms() * 2);
+  const int grid = std::min<int>((map->dev.max_blocks + kCallBlocks - 1) / kCallBlocks, num_sms() * 2);
   COVOX_LAUNCH(kKMerge, s, merge_kernel<<<grid, kTileThreads, 0, s>>>(map->dev));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
@@ -564,21 +606,51 @@ cvx_status cvx_extract_blocks(cvx_submap* map, int64_t capacity, int32_t* keys, 
   return CVX_OK;
 }
 
+cvx_status cvx_reset_submaps(cvx_submap* const* maps, int32_t n, void* stream) {
+  if (n < 0 || (n > 0 && !maps)) return CVX_ERR_INVALID_ARG;
+  for (int q = 0; q < n; ++q)
+    if (!maps[q]) return CVX_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int q0 = 0; q0 < n; q0 += kResetMaps) {
+    ResetBatch rb;
+    std::memset(&rb, 0, sizeof(rb));
+    rb.n = std::min(kResetMaps, n - q0);
+    long long work = 0;
+    for (int k = 0; k < rb.n; ++k) {
+      cvx_submap* map = maps[q0 + k];
+      map->last_stream = s;
+      if (flush_pending(map, s, true) != CVX_OK) return CVX_ERR_CUDA;
+      ResetDesc& d = rb.m[k];
+      d.keys = map->dev.keys;
+      d.vals = map->dev.vals;
+      d.st = map->dev.st;
+      d.D = (uint4*)map->dev.D;
+      d.W = (uint4*)map->dev.W;
+      d.C = (uint4*)map->dev.C;
+      for (int k2 = 0; k2 < map->n_sets; ++k2) {
+        const SubmapDev& v = set_view(map, k2);
+        d.acc[k2] = (float4*)v.acc;
+        d.cacc[k2] = v.cacc;
+        d.tepoch[k2] = v.tepoch;
+        d.gep[k2] = (uint32_t*)v.gep;
+      }
+      d.slots = map->p.hash_slots;
+      d.max_blocks = map->dev.max_blocks;
+      d.n_sets = map->n_sets;
+      d.plane16 = (int)(kVoxPerBlock * map->bytes_per_vox / 16);
+      work += d.slots + (long long)d.max_blocks * d.plane16;
+    }
+    // enough CTAs for the largest possible reset, at most four per SM
+    const int grid = (int)std::max<long long>(1, std::min<long long>(4ll * num_sms(), work / 4096 + 1));
+    COVOX_LAUNCH(kKZeroPool, s, reset_pools_kernel<<<grid, 256, 0, s>>>(rb));
+    COVOX_LAUNCH(kKDiscard, s, reset_states_kernel<<<1, 256, 0, s>>>(rb));
+  }
+  return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
+}
+
 cvx_status cvx_reset_submap(cvx_submap* map, void* stream) {
   if (!map) return CVX_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  map->last_stream = s;
-  if (flush_pending(map, s, true) != CVX_OK) return CVX_ERR_CUDA;
-  SetViews sv;
-  for (int k = 0; k < 4; ++k) sv.v[k] = set_view(map, k < map->n_sets ? k : 0);
-  COVOX_LAUNCH(kKDiscard, s, discard_sums_kernel<<<num_sms(), 256, 0, s>>>(sv, map->n_sets));
-  const int bpb = (int)(kVoxPerBlock * map->bytes_per_vox);
-  COVOX_LAUNCH(kKZeroPool, s, zero_pool_kernel<<<num_sms() * 4, 256, 0, s>>>(map->dev, bpb));
-  cudaMemsetAsync(map->dev.keys, 0xff, (size_t)map->p.hash_slots * 8, s);
-  cudaMemsetAsync(map->dev.vals, 0xff, (size_t)map->p.hash_slots * 4, s);
-  for (int k = 0; k < map->n_sets; ++k) cudaMemsetAsync(set_view(map, k).tepoch, 0, (size_t)map->p.max_blocks * 4, s);
-  cudaMemsetAsync(map->dev.st, 0, sizeof(State), s);
-  return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
+  return cvx_reset_submaps(&map, 1, stream);
 }
 
 cvx_status cvx_submap_counters(cvx_submap* map, cvx_counters* out) {

@@ -23,6 +23,11 @@ constexpr int kTileBlocks = 64;      // distinct blocks recorded per tile (power
 constexpr int kMapDead = -3;         // vals[] marker: block unusable (pool exhausted)
 constexpr long long kSpinLimit = 1 << 20;   // polls of an unpublished slot (~1 s)
 
+// Touch tag of scan epoch ep in the per-group tags (never 0, the cleared
+// value).  Tags repeat every 255 scans: a stale tag equal to the current one
+// only makes a merge read a group whose sums are zero.
+__device__ __forceinline__ uint8_t group_tag(uint32_t ep) { return (uint8_t)(1u + ep % 255u); }
+
 // Global activation of one block ("activate", Sec. III-B: insert-or-find,
 // pool index by atomic bump for a new block), and its mark as touched by the
 // scan: the block's touch epoch is set to the scan's epoch `ep` (a plain
@@ -301,6 +306,32 @@ __device__ __forceinline__ int local_slot(const TileSmem& t, int lb, unsigned lo
   return -1;
 }
 
+// Flush of a tile's shared sums (kLocal) into its blocks' per-scan sums:
+// every voxel with a nonzero weight sum by one vector reduction, and the
+// touch tag of each group holding one.
+__device__ __forceinline__ void flush_slots(const SubmapDev& m, const TileSmem& t, int lb, const Fixed& fx,
+                                            uint8_t tag) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int q = 0; q < lb; ++q) {
+    const int pool = t.pool[q];
+    if (pool < 0) continue;
+    float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
+    for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
+      const int e = q * kVoxPerBlock + v;
+      bool nz = (t.lo_w[e] | (unsigned)t.hi_w[e]) != 0u;
+      if (nz) {
+        const float w = fixed_value(t.lo_w[e], t.hi_w[e], fx.S, fx.inv_scale);
+        const float wd = fixed_value(t.lo_wd[e], t.hi_wd[e], fx.S, fx.inv_scale);
+        nz = w != 0.0f;
+        if (nz) red_add2(dst + v, wd, w);
+      }
+      // lanes 4j .. 4j + 3 hold the voxels of one group
+      const unsigned bal = __ballot_sync(0xffffffffu, nz);
+      if ((lane & 3) == 0 && ((bal >> lane) & 0xFu)) m.gep[(size_t)pool * kGroupsPerBlock + (v >> 2)] = tag;
+    }
+  }
+}
+
 // The general form of the tile phase, one point after another per thread:
 // any band length, and free-space carving (rays from the sensor origin, with
 // the distance recomputed exactly near the band).  Scans without carving and
@@ -355,6 +386,7 @@ __device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& 
   __syncthreads();
 
   const float inv_drop = 1.0f / (m.trunc - m.vs);
+  const uint8_t tag = group_tag(ep);
   unsigned n_obs = 0, n_valid = 0;
   for (int k = 0; k < iters; ++k) {
     const long long i = tp.point(sc, k);
@@ -393,6 +425,7 @@ __device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& 
       slot_end = kLocal ? local_slot(t, lb, key_end) : -1;
       gpool_end = slot_end < 0 ? cached_pool(m, t, key_end, ep) : -1;
     }
+    int last_g = -1;   // group of the previous cell (the group changes at every block crossing)
     for (;;) {
       const float dc = fminf(fmaxf(dist, -m.trunc), m.trunc);
       float w = w0;
@@ -407,7 +440,9 @@ __device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& 
       } else if (gpool >= 0) {
         red_add2(m.acc + (size_t)gpool * kVoxPerBlock + l, w * (dc - m.trunc), w);
         if (sc.rgb) red_add4(m.cacc + (size_t)gpool * kVoxPerBlock + l, w * col[0], w * col[1], w * col[2]);
+        if ((l >> 2) != last_g) m.gep[(size_t)gpool * kGroupsPerBlock + (l >> 2)] = tag;
       }
+      last_g = l >> 2;
       if (d.left == 0) break;
       // next axis: the traversal rule of Dda::step, as selects
       const bool a0 = d.v[0] != d.e[0], a1 = d.v[1] != d.e[1], a2 = d.v[2] != d.e[2];
@@ -451,19 +486,7 @@ __device__ inline void integrate_tile_legacy(const SubmapDev& m, const ScanDev& 
       t.pool[q] = key == kEmptyKey ? -1 : cached_pool(m, t, key, ep);
     }
     __syncthreads();
-    // flush the tile's sums into the per-scan accumulators
-    for (int q = 0; q < lb; ++q) {
-      const int pool = t.pool[q];
-      if (pool < 0) continue;
-      float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
-      for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
-        const int e = q * kVoxPerBlock + v;
-        if ((t.lo_w[e] | (unsigned)t.hi_w[e]) == 0u) continue;
-        const float w = fixed_value(t.lo_w[e], t.hi_w[e], fx.S, fx.inv_scale);
-        const float wd = fixed_value(t.lo_wd[e], t.hi_wd[e], fx.S, fx.inv_scale);
-        if (w != 0.0f) red_add2(dst + v, wd, w);
-      }
-    }
+    flush_slots(m, t, lb, fx, tag);   // the tile's sums into the per-scan accumulators
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -653,6 +676,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
 
   const float inv_drop = 1.0f / (m.trunc - m.vs);
   const float INF = __int_as_float(0x7f800000);
+  const uint8_t tag = group_tag(ep);
   unsigned n_obs = 0, n_valid = 0;
   int* list = t.list + (tid >> 5) * kListPerWarp;
   for (int k0 = 0; k0 < iters; k0 += kGather) {
@@ -702,6 +726,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
       if (twom) warp_lookup<kLocal>(m, t, lb, ep, twom, two, key_end, slot_end, pool_end);
       if (!act) continue;
       // traversal: one observation per cell
+      int last_g = -1;   // group of the previous cell (the group changes at every block crossing)
       for (;;) {
         const float dc = fminf(fmaxf(w.dist, -m.trunc), m.trunc);
         float wt = w0;
@@ -715,7 +740,9 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
           fixed_add(t.lo_w + e, t.hi_w + e, fx.S, __float2ll_rn(wt * fx.scale));
         } else if (pool >= 0) {
           red_add2(m.acc + (size_t)pool * kVoxPerBlock + w.l, wt * (dc - m.trunc), wt);
+          if ((w.l >> 2) != last_g) m.gep[(size_t)pool * kGroupsPerBlock + (w.l >> 2)] = tag;
         }
+        last_g = w.l >> 2;
         if (w.left == 0) break;
         --w.left;
         const bool p1 = w.tm1 < w.tm0;
@@ -757,19 +784,7 @@ __device__ inline void integrate_tile_t(const SubmapDev& m, const ScanDev& sc, i
       t.pool[q] = key == kEmptyKey ? -1 : cached_pool(m, t, key, ep);
     }
     __syncthreads();
-    // flush the tile's sums into the per-scan accumulators
-    for (int q = 0; q < lb; ++q) {
-      const int pool = t.pool[q];
-      if (pool < 0) continue;
-      float2* dst = m.acc + (size_t)pool * kVoxPerBlock;
-      for (int v = tid; v < kVoxPerBlock; v += kTileThreads) {
-        const int e = q * kVoxPerBlock + v;
-        if ((t.lo_w[e] | (unsigned)t.hi_w[e]) == 0u) continue;
-        const float w = fixed_value(t.lo_w[e], t.hi_w[e], fx.S, fx.inv_scale);
-        const float wd = fixed_value(t.lo_wd[e], t.hi_wd[e], fx.S, fx.inv_scale);
-        if (w != 0.0f) red_add2(dst + v, wd, w);
-      }
-    }
+    flush_slots(m, t, lb, fx, tag);   // the tile's sums into the per-scan accumulators
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -844,7 +859,78 @@ __device__ __forceinline__ void integrate_tile_v(const SubmapDev& m, const ScanD
 }
 
 // ------------------------------------------------------------- merge
-constexpr int kMergeThreads = 128;   // 4 voxels per thread
+// Merge of one scan's sums into D and W, group by group.  A CTA of 256
+// threads merges the blocks of eight spans of kSpanBlocks consecutive pool
+// indices (one span per warp; the spans strided, so that touched blocks that
+// cluster in pool order spread over the CTAs of a merge) in three steps,
+// each one round of independent loads:
+//   1. the spans' touch epochs: the blocks holding the scan's epoch `ep`
+//      (the stream compaction of the allocation pass, Sec. III-D) are
+//      compacted into a list;
+//   2. the touch tags of those blocks' groups (16 per thread): the groups
+//      holding the scan's tag are compacted into a list of (block, group)
+//      items, at most 16 per thread;
+//   3. the items, one per thread at a time: the group's sums, D and W
+//      loaded together, D <- (D W + sum w d)/(W + sum w), W <- min(W + sum
+//      w, max_weight) for its voxels with sum w > 0 (and the colour update
+//      of colour submaps), stores, and the group's sums cleared.
+// skip (the scan had a device error): the sums are only cleared.
+constexpr int kSpanBlocks = 32;                  // blocks of one span (one warp's epochs)
+constexpr int kSpansPerCall = kTileThreads / 32; // spans one merge_span call covers
+constexpr int kCallBlocks = kSpanBlocks * kSpansPerCall;
+constexpr int kTagChunks = kGroupsPerBlock / 16; // 16-byte chunks of a block's tags
+constexpr int kMergeItems = 16 * kTileThreads;   // items of one round of tag chunks
+
+struct MergeSmem {
+  int* pool;              // [kCallBlocks] touched blocks of the spans
+  unsigned short* item;   // [kMergeItems] (index into pool) << 7 | group
+  int* wsum;              // [kTileThreads / 32] per-warp partial sums
+};
+
+struct MergeSmemStatic {
+  int pool[kCallBlocks];
+  unsigned short item[kMergeItems];
+  int wsum[kTileThreads / 32];
+  __device__ MergeSmem view() { return MergeSmem{pool, item, wsum}; }
+};
+
+// The merge's lists inside a tile CTA's dynamic shared memory (any lb): a
+// CTA runs either a tile or a merge at a time.
+__device__ inline MergeSmem merge_smem(char* smem) {
+  const TileSmem t = tile_smem(smem, 0);
+  static_assert(kCache * 8 >= kCallBlocks * 4, "touched-block list fits the block cache");
+  static_assert((kTileThreads / 32) * kListPerWarp * 4 >= kMergeItems * 2, "item list fits the point lists");
+  return MergeSmem{reinterpret_cast<int*>(t.ckey), reinterpret_cast<unsigned short*>(t.list),
+                   reinterpret_cast<int*>(t.red)};
+}
+
+// Exclusive prefix sum of v over the CTA; *total gets the sum (every thread).
+__device__ __forceinline__ int cta_exclusive_scan(int v, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int off = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kTileThreads / 32; ++w) {
+    const int t = wsum[w];
+    off += w < warp ? t : 0;
+    tot += t;
+  }
+  __syncthreads();   // wsum is reused by the next scan
+  *total = tot;
+  return off + x - v;
+}
+
+// Bits of the bytes of w equal to the byte in every lane of t4 (byte k -> bit k).
+__device__ __forceinline__ uint32_t tag_bits4(uint32_t w, uint32_t t4) {
+  return ((__vcmpeq4(w, t4) & 0x01010101u) * 0x01020408u) >> 24;
+}
 
 template <int kStore>
 struct Vox4;
@@ -888,96 +974,46 @@ struct Vox4<1> {   // FP16 storage: D / trunc and W as IEEE half, FP32 arithmeti
   }
 };
 
-// Merge the sums of blocks p0 and p1 (pool indices; p1 < 0: none) with
-// kMergeThreads threads, this one being `tid` (4 voxels of each block).  All
-// loads of both blocks are issued before any result is used, so two blocks'
-// dependent chains overlap.  Sums, D and W are read from the L2 (.cg): in the
-// persistent kernels they were last written by other SMs.  Returns the
-// voxels merged by this thread.
+// One group's loaded values: its sums (sum w (d - trunc), sum w per voxel),
+// and D, W.
+struct GroupVals {
+  float4 s0, s1;
+  float D[4], W[4];
+};
+
 template <int kStore>
-__device__ __forceinline__ int merge_pools(const SubmapDev& m, int p0, int p1, bool skip, int tid) {
-  float4* a = reinterpret_cast<float4*>(m.acc + (size_t)p0 * kVoxPerBlock) + 2 * tid;
-  float4* b = p1 >= 0 ? reinterpret_cast<float4*>(m.acc + (size_t)p1 * kVoxPerBlock) + 2 * tid : nullptr;
-  const float4 a0 = __ldcg(a), a1 = __ldcg(a + 1);
-  float4 b0 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = b0;
-  if (b) {
-    b0 = __ldcg(b);
-    b1 = __ldcg(b + 1);
-  }
-  const float swa[4] = {a0.x, a0.z, a1.x, a1.z}, wa[4] = {a0.y, a0.w, a1.y, a1.w};
-  const float swb[4] = {b0.x, b0.z, b1.x, b1.z}, wb[4] = {b0.y, b0.w, b1.y, b1.w};
-  const bool ta = (wa[0] != 0.f) | (wa[1] != 0.f) | (wa[2] != 0.f) | (wa[3] != 0.f);
-  const bool tb = (wb[0] != 0.f) | (wb[1] != 0.f) | (wb[2] != 0.f) | (wb[3] != 0.f);
-  const size_t ea = (size_t)p0 * kVoxPerBlock + 4 * tid, eb = (size_t)(p1 >= 0 ? p1 : 0) * kVoxPerBlock + 4 * tid;
-  float Da[4], Wa[4], Db[4], Wb[4];
-  if (ta && !skip) Vox4<kStore>::load(m, ea, Da, Wa);
-  if (tb && !skip) Vox4<kStore>::load(m, eb, Db, Wb);
-  int merged = 0;
-  if (ta) {
-    if (!skip) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (wa[q] != 0.0f) {
-          const float wn = Wa[q] + wa[q];
-          Da[q] = m.trunc + ((Da[q] - m.trunc) * Wa[q] + swa[q]) / wn;
-          Wa[q] = fminf(wn, m.max_w);
-          ++merged;
-        }
-      Vox4<kStore>::store(m, ea, Da, Wa);
-    }
-    a[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    a[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  if (tb) {
-    if (!skip) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (wb[q] != 0.0f) {
-          const float wn = Wb[q] + wb[q];
-          Db[q] = m.trunc + ((Db[q] - m.trunc) * Wb[q] + swb[q]) / wn;
-          Wb[q] = fminf(wn, m.max_w);
-          ++merged;
-        }
-      Vox4<kStore>::store(m, eb, Db, Wb);
-    }
-    b[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    b[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  return merged;
+__device__ __forceinline__ void load_group(const SubmapDev& m, size_t e, bool skip, GroupVals& g) {
+  const float4* a = reinterpret_cast<const float4*>(m.acc + e);
+  g.s0 = __ldcg(a);
+  g.s1 = __ldcg(a + 1);
+  if (!skip) Vox4<kStore>::load(m, e, g.D, g.W);
 }
 
-// Colour update of this thread's 4 voxels of block `pool` (colour submaps),
-// run before the block's D/W merge by the same thread: C <- (C W + S_wc) /
-// (W + S_w) wherever S_w != 0, W being the stored weight before the merge
-// (the same rule as D); the block's colour sums are cleared.  skip: clear only.
-template <int kStore>
-__device__ __forceinline__ void merge_colour(const SubmapDev& m, int pool, bool skip, int tid) {
-  const size_t e = (size_t)pool * kVoxPerBlock + 4 * tid;
-  const float4* a = reinterpret_cast<const float4*>(m.acc + e);
-  const float4 a0 = __ldcg(a), a1 = __ldcg(a + 1);
-  const float sw[4] = {a0.y, a0.w, a1.y, a1.w};
-  if (sw[0] == 0.f && sw[1] == 0.f && sw[2] == 0.f && sw[3] == 0.f) return;   // its colour sums are zero too
+// Colour update of one group (colour submaps), before its D/W merge: C <- (C W
+// + S_wc) / (W + S_w) wherever S_w != 0, W being the stored weight before the
+// merge (the same rule as D); the group's colour sums are cleared.
+__device__ __forceinline__ void merge_colour_group(const SubmapDev& m, size_t e, const GroupVals& g, bool skip) {
   float4* cs = m.cacc + e;
   if (!skip) {
-    float4 s[4];
+    const float sw[4] = {g.s0.y, g.s0.w, g.s1.y, g.s1.w};
+    float4 c4[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) s[q] = __ldcg(cs + q);
-    float D[4], W[4];
-    Vox4<kStore>::load(m, e, D, W);
-    float* cp = m.C + (size_t)pool * 3 * kVoxPerBlock + 4 * tid;
+    for (int q = 0; q < 4; ++q) c4[q] = __ldcg(cs + q);
+    const size_t pool = e / kVoxPerBlock, v = e % kVoxPerBlock;
+    float* cp = m.C + pool * 3 * kVoxPerBlock + v;
     float4 c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) c[k] = __ldcg(reinterpret_cast<const float4*>(cp + k * kVoxPerBlock));
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (sw[q] == 0.f) continue;
-      const float wn = W[q] + sw[q];
+      const float wn = g.W[q] + sw[q];
       float* r = reinterpret_cast<float*>(&c[0]) + q;
-      float* g = reinterpret_cast<float*>(&c[1]) + q;
+      float* gr = reinterpret_cast<float*>(&c[1]) + q;
       float* b = reinterpret_cast<float*>(&c[2]) + q;
-      *r = (*r * W[q] + s[q].x) / wn;
-      *g = (*g * W[q] + s[q].y) / wn;
-      *b = (*b * W[q] + s[q].z) / wn;
+      *r = (*r * g.W[q] + c4[q].x) / wn;
+      *gr = (*gr * g.W[q] + c4[q].y) / wn;
+      *b = (*b * g.W[q] + c4[q].z) / wn;
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) *reinterpret_cast<float4*>(cp + k * kVoxPerBlock) = c[k];
@@ -986,49 +1022,92 @@ __device__ __forceinline__ void merge_colour(const SubmapDev& m, int pool, bool 
   for (int q = 0; q < 4; ++q) cs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Merge of a span of kSpanBlocks consecutive pool indices [p0, p0 + n) by a
-// 256-thread CTA: the span's touch epochs are read in one round (.cg), the
-// blocks holding the scan's epoch `ep` compacted into shared memory with a
-// warp ballot, then merged two per half CTA.  Returns this thread's merged
-// voxels; *touched (every thread) gets the span's touched blocks.  kColour:
-// the colour update of colour submaps is compiled in (kernels whose scans
-// include no colour scan, and so no colour submap, leave it out).
-constexpr int kSpanBlocks = 32;
-
-struct SpanList {
-  int pool[kSpanBlocks];
-  int n;
-};
-
-template <bool kColour = true>
-__device__ __forceinline__ int merge_span(const SubmapDev& m, int p0, int n, uint32_t ep, bool skip, SpanList* sl,
-                                          int* touched) {
-  const int tid = threadIdx.x;
-  if (tid < 32) {
-    const bool t = tid < n && __ldcg(m.tepoch + p0 + tid) == ep;
-    const unsigned bal = __ballot_sync(0xffffffffu, t);
-    if (t) sl->pool[__popc(bal & ((1u << tid) - 1u))] = p0 + tid;
-    if (tid == 0) sl->n = __popc(bal);
-  }
-  __syncthreads();
-  const int cnt = sl->n;
-  const int half = tid / kMergeThreads, sub = tid % kMergeThreads;
+// Merge of one loaded group; returns its merged voxels.
+template <int kStore, bool kColour>
+__device__ __forceinline__ int merge_group(const SubmapDev& m, size_t e, GroupVals& g, bool skip) {
+  const float sw[4] = {g.s0.x, g.s0.z, g.s1.x, g.s1.z}, w[4] = {g.s0.y, g.s0.w, g.s1.y, g.s1.w};
+  if (w[0] == 0.f && w[1] == 0.f && w[2] == 0.f && w[3] == 0.f) return 0;   // weight-0 observations only
+  if (kColour && m.C) merge_colour_group(m, e, g, skip);
   int merged = 0;
-  for (int k = 2 * half; k < cnt; k += 4) {
-    const int q = k + 1 < cnt ? sl->pool[k + 1] : -1;
-    if (kColour && m.C) {
-      if (m.storage == 0) {
-        merge_colour<0>(m, sl->pool[k], skip, sub);
-        if (q >= 0) merge_colour<0>(m, q, skip, sub);
-      } else {
-        merge_colour<1>(m, sl->pool[k], skip, sub);
-        if (q >= 0) merge_colour<1>(m, q, skip, sub);
+  if (!skip) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (w[q] != 0.0f) {
+        const float wn = g.W[q] + w[q];
+        g.D[q] = m.trunc + ((g.D[q] - m.trunc) * g.W[q] + sw[q]) / wn;
+        g.W[q] = fminf(wn, m.max_w);
+        ++merged;
       }
-    }
-    merged += m.storage == 0 ? merge_pools<0>(m, sl->pool[k], q, skip, sub) : merge_pools<1>(m, sl->pool[k], q, skip, sub);
+    Vox4<kStore>::store(m, e, g.D, g.W);
   }
+  float4* a = reinterpret_cast<float4*>(m.acc + e);
+  a[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+  a[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+  return merged;
+}
+
+// The listed items, one per thread at a time: the group's sums, D and W
+// are loaded together.  (Two items in flight per thread cost spills in the
+// tile code of the kernels that hold both phases.)
+template <int kStore, bool kColour>
+__device__ __forceinline__ int merge_items(const SubmapDev& m, const MergeSmem& ms, int n_items, bool skip) {
+  int merged = 0;
+  for (int i = threadIdx.x; i < n_items; i += kTileThreads) {
+    const unsigned it = ms.item[i];
+    const size_t e = (size_t)ms.pool[it >> 7] * kVoxPerBlock + 4 * (it & 127u);
+    GroupVals g;
+    load_group<kStore>(m, e, skip, g);
+    merged += merge_group<kStore, kColour>(m, e, g, skip);
+  }
+  return merged;
+}
+
+// Merge of the spans span0 + w * step (w = 0 .. kSpansPerCall - 1, warp w
+// takes span w) of a submap with nb allocated blocks.  Returns this thread's
+// merged voxels; *touched (every thread) gets the spans' touched blocks.
+// kColour: the colour update of colour submaps is compiled in (kernels whose
+// scans include no colour scan, and so no colour submap, leave it out).
+template <bool kColour = true>
+__device__ __forceinline__ int merge_span(const SubmapDev& m, int span0, int step, int nb, uint32_t ep, bool skip,
+                                          const MergeSmem& ms, int* touched) {
+  const int tid = threadIdx.x;
+  const long long p = (long long)(span0 + (tid >> 5) * step) * kSpanBlocks + (tid & 31);
+  const bool t = p < nb && __ldcg(m.tepoch + p) == ep;
+  int cnt = 0;
+  const int o = cta_exclusive_scan(t ? 1 : 0, ms.wsum, &cnt);
+  if (t) ms.pool[o] = (int)p;
   *touched = cnt;
-  __syncthreads();   // the list is rewritten by the next span
+  if (cnt == 0) return 0;   // uniform over the CTA
+  __syncthreads();
+  const uint8_t tag = group_tag(ep);
+  const uint32_t t4 = 0x01010101u * tag;
+  const int n_chunks = cnt * kTagChunks;
+  const uint4* tags = reinterpret_cast<const uint4*>(m.gep);
+  // the next round's tag chunk is loaded while the current round is merged
+  uint4 next = make_uint4(0u, 0u, 0u, 0u);
+  if (tid < n_chunks) next = __ldcg(tags + (size_t)ms.pool[tid / kTagChunks] * kTagChunks + tid % kTagChunks);
+  int merged = 0;
+  for (int c0 = 0; c0 < n_chunks; c0 += kTileThreads) {
+    const int c = c0 + tid;
+    const uint4 g = next;
+    const int cn = c + kTileThreads;
+    if (cn < n_chunks) next = __ldcg(tags + (size_t)ms.pool[cn / kTagChunks] * kTagChunks + cn % kTagChunks);
+    uint32_t bits = 0;
+    if (c < n_chunks)
+      bits = tag_bits4(g.x, t4) | (tag_bits4(g.y, t4) << 4) | (tag_bits4(g.z, t4) << 8) | (tag_bits4(g.w, t4) << 12);
+    int n_items = 0;
+    int k = cta_exclusive_scan(__popc(bits), ms.wsum, &n_items);
+    const unsigned base = (unsigned)(c / kTagChunks) << 7 | (unsigned)(c % kTagChunks) * 16u;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      ms.item[k++] = (unsigned short)(base + b);
+    }
+    __syncthreads();
+    merged += m.storage == 0 ? merge_items<0, kColour>(m, ms, n_items, skip)
+                             : merge_items<1, kColour>(m, ms, n_items, skip);
+    __syncthreads();   // the item list is rewritten by the next round
+  }
   return merged;
 }
 

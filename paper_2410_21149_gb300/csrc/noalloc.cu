@@ -6,7 +6,8 @@
 // process's allocator.  For them,
 // cvx_integrate_scan_noalloc() integrates a scan into submap storage the
 // caller already owns (a cvx_submap_view) and keeps its per-scan scratch (the
-// per-voxel sums and the blocks' touch epochs) in one file-scope device array
+// per-voxel sums, the blocks' touch epochs and their groups' touch tags) in
+// one file-scope device array
 // of fixed size.  It runs the same device functions as cvx_integrate_scan.
 //
 // The scratch array is a host-side symbol in host code: its device address is
@@ -31,9 +32,10 @@ namespace {
 
 constexpr size_t kAccBytes = (size_t)CVX_NOALLOC_MAX_BLOCKS * kVoxPerBlock * sizeof(float2);
 constexpr size_t kEpochBytes = (size_t)CVX_NOALLOC_MAX_BLOCKS * sizeof(uint32_t);
-constexpr size_t kScratchBytes = kAccBytes + kEpochBytes;
+constexpr size_t kTagBytes = (size_t)CVX_NOALLOC_MAX_BLOCKS * kGroupsPerBlock;
+constexpr size_t kScratchBytes = kAccBytes + kEpochBytes + kTagBytes;
 
-// per-scan sums | touch epochs of the blocks
+// per-scan sums | touch epochs of the blocks | touch tags of their groups
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 static_assert(sizeof(State) <= CVX_SUBMAP_STATE_BYTES, "state buffer too small");
@@ -79,13 +81,13 @@ __global__ void __launch_bounds__(kTileThreads) integrate_static_kernel(SubmapDe
 // The scan's epoch is 1: the touch epochs are cleared before every call.
 __global__ void __launch_bounds__(kTileThreads) merge_static_kernel(SubmapDev m) {
   __shared__ unsigned long long red[kTileThreads / 32];
-  __shared__ SpanList sl;
+  __shared__ MergeSmemStatic sl;
   const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
   const bool skip = *((volatile int32_t*)m.frame_err) != 0;
   unsigned long long merged = 0, touched = 0;
-  for (int p0 = blockIdx.x * kSpanBlocks; p0 < nb; p0 += gridDim.x * kSpanBlocks) {
+  for (int span = blockIdx.x; span * kSpanBlocks < nb; span += kSpansPerCall * gridDim.x) {
     int t = 0;
-    merged += merge_span(m, p0, min(kSpanBlocks, nb - p0), 1u, skip, &sl, &t);
+    merged += merge_span(m, span, gridDim.x, nb, 1u, skip, sl.view(), &t);
     touched += t;
   }
 #pragma unroll
@@ -159,6 +161,7 @@ extern "C" cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, co
   unsigned char* base = (unsigned char*)scratch;
   m.acc = (float2*)base;
   m.tepoch = (uint32_t*)(base + kAccBytes);
+  m.gep = base + kAccBytes + kEpochBytes;
   m.slot_mask = (uint32_t)(view->hash_slots - 1);
   m.max_probe = (int)(view->hash_slots < 4096 ? view->hash_slots : 4096);
   m.max_blocks = (int)view->max_blocks;
@@ -170,11 +173,12 @@ extern "C" cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, co
 
   cudaStream_t s = (cudaStream_t)stream;
   // The scratch keeps the previous call's contents: clear the sums, the
-  // touch epochs and this scan's fields of the caller's state (error bits,
+  // touch epochs, the group tags and this scan's fields of the caller's state (error bits,
   // merge ticket, epoch: the scan's epoch is 1).
   const size_t acc_bytes = (size_t)view->max_blocks * kVoxPerBlock * sizeof(float2);
   if (cudaMemsetAsync(m.acc, 0, acc_bytes, s) != cudaSuccess ||
       cudaMemsetAsync(m.tepoch, 0, (size_t)view->max_blocks * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(m.gep, 0, (size_t)view->max_blocks * kGroupsPerBlock, s) != cudaSuccess ||
       cudaMemsetAsync((char*)view->state + offsetof(State, frame_err), 0, sizeof(int32_t), s) != cudaSuccess ||
       cudaMemsetAsync((char*)view->state + offsetof(State, ticket), 0, sizeof(uint32_t), s) != cudaSuccess ||
       cudaMemsetAsync((char*)view->state + offsetof(State, epoch), 0, sizeof(uint32_t), s) != cudaSuccess) {
@@ -184,7 +188,7 @@ extern "C" cvx_status cvx_integrate_scan_noalloc(const cvx_submap_view* view, co
   if (n == 0) return CVX_OK;
   COVOX_LAUNCH(kKAccum, s,
                integrate_static_kernel<<<sc.n_tiles, kTileThreads, tile_smem_bytes(lb), s>>>(m, sc, lb));
-  const int spans = (m.max_blocks + kSpanBlocks - 1) / kSpanBlocks;
+  const int spans = (m.max_blocks + kCallBlocks - 1) / kCallBlocks;
   const int grid = spans < num_sms() * 2 ? spans : num_sms() * 2;
   COVOX_LAUNCH(kKMerge, s, merge_static_kernel<<<grid, kTileThreads, 0, s>>>(m));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;

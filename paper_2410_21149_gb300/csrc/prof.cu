@@ -10,11 +10,11 @@
 namespace {
 
 const char* kNames[covox::kNumKinds] = {"alloc_kernel",    "integrate_kernel", "merge_kernel",
-                                        "zero_pool_kernel", "batched_kernel", "features_kernel",
+                                        "reset_pools_kernel", "batched_kernel", "features_kernel",
                                         "mlp_fwd_kernel",  "mlp_bwd_kernel", "adam_kernel",
                                         "targets_kernel", "integrate_pipelined_kernel", "flush_kernel",
                                         "pipe_close_kernel", "esdf_kernels",
-                                        "hash_kernels", "discard_sums_kernel", "point_weights_kernel"};
+                                        "hash_kernels", "reset_states_kernel", "point_weights_kernel"};
 
 struct Rec {
   int kind;

@@ -11,7 +11,7 @@ enum KernelKind : int {
   kKAlloc = 0,      // block activation / allocation pass
   kKAccum = 1,      // per-scan observation accumulation
   kKMerge = 2,      // per-block merge into D, W
-  kKZeroPool = 3,   // reset of the block pool
+  kKZeroPool = 3,   // reset: hash, block pool, touch epochs, unmerged sums
   kKBatched = 4,    // persistent batched integration
   kKFeatures = 5,   // per-point features of the weight model
   kKMlpFwd = 6,     // weight model forward
@@ -23,7 +23,7 @@ enum KernelKind : int {
   kKPipeClose = 12, // pipelined per-scan bookkeeping after each scan
   kKEsdf = 13,      // distance field of a submap
   kKHash = 14,      // stand-alone block hash insert / find
-  kKDiscard = 15,   // reset: per-scan sums a launch left unmerged
+  kKDiscard = 15,   // reset: the submaps' state words
   kKPointWeights = 16,   // fused features + weight network of organised scans
   kNumKinds = 17
 };

@@ -92,3 +92,69 @@ def test_batched_single_submap_many_frames_four_sets():
         compare(g, o, 1e-5)
         assert g[3]["frames"] == 12 and g[3]["observations"] == o[3]["obs"]
 
+
+
+def test_reset_many_submaps_then_reintegrate(mixed):
+    """cvx_reset_submaps over 6 mixed submaps after a batched launch (and over
+    50 more, past one launch's 48) leaves empty submaps with zero counters, and
+    integrating again gives the oracle's result, as for fresh submaps."""
+    import torch
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import _capi
+    from _harness import int_params
+    storages = [m % 2 for m in range(len(mixed.submaps))]
+    subs = [cvx.Submap(sm.voxel_size, sm.trunc, mixed.max_weight, st, max_blocks=1 << 16, sets=4)
+            for sm, st in zip(mixed.submaps, storages)]
+    keep, scans = [], []
+    for m, sm in enumerate(mixed.submaps):
+        for sc in sm.scans:
+            pts = torch.from_numpy(np.ascontiguousarray(sc.points)).cuda()
+            keep.append(pts)
+            scans.append((m, pts, sc.T_sub_sensor, None, int_params(mixed, sc)))
+    handles = [s.handle for s in subs]
+    batch = _capi.cvx_batch_create(len(subs), len(scans))
+    for rep in range(2):
+        _capi.cvx_integrate_batch(batch, handles, scans)
+        _capi.cvx_reset_submaps(handles)
+        torch.cuda.synchronize()
+        for s in subs:
+            c = s.counters()
+            assert s.num_blocks() == 0 and c["frames"] == 0 and c["observations"] == 0 and s.status() == 0
+    _capi.cvx_integrate_batch(batch, handles, scans)
+    torch.cuda.synchronize()
+    assert _capi.cvx_batch_error(batch) == 0
+    for m, (sm, sub, st) in enumerate(zip(mixed.submaps, subs, storages)):
+        keys, D, W = (t.cpu().numpy() for t in sub.extract())
+        D = D.astype(np.float64) * (np.float64(np.float32(sm.trunc)) if st else 1.0)
+        one = sg.Workload(mixed.name, [sm], mixed.max_weight, mixed.weight_mode, mixed.dropoff,
+                          mixed.min_range, mixed.max_range, mixed.scene, st)
+        o = run_oracle(one, fp16=bool(st))[0]
+        g = (keys, D, W.astype(np.float64), sub.counters(), sub.status())
+        if st:
+            compare(g, o, 1e-3 * sm.trunc, fp16_trunc=sm.trunc)
+        else:
+            compare(g, o, 1e-5)
+    _capi.cvx_batch_destroy(batch)
+    for s in subs:
+        s.close()
+    # more submaps than one reset launch covers
+    wl = sg.make_c1(n_frames=1)
+    sm = wl.submaps[0]
+    pts = torch.from_numpy(np.ascontiguousarray(sm.scans[0].points)).cuda()
+    many = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, m % 2, max_blocks=1 << 10) for m in range(50)]
+    for s in many:
+        s.integrate(pts, sm.scans[0].T_sub_sensor, int_params(wl, sm.scans[0]))
+    assert all(s.num_blocks() > 0 for s in many)
+    _capi.cvx_reset_submaps([s.handle for s in many])
+    assert all(s.num_blocks() == 0 and s.counters()["valid_points"] == 0 for s in many)
+    s = many[49]
+    s.integrate(pts, sm.scans[0].T_sub_sensor, int_params(wl, sm.scans[0]))
+    keys, D, W = (t.cpu().numpy() for t in s.extract())
+    o = run_oracle(sg.Workload(wl.name, [sm], wl.max_weight, wl.weight_mode, wl.dropoff, wl.min_range,
+                               wl.max_range, wl.scene, 1), fp16=True)[0]
+    compare((keys, D.astype(np.float64) * np.float64(np.float32(sm.trunc)), W.astype(np.float64), s.counters(),
+             s.status()), o, 1e-3 * sm.trunc, fp16_trunc=sm.trunc)
+    for s in many:
+        s.close()
+    with pytest.raises(_capi.CovoxError):
+        _capi.cvx_reset_submaps([0])
