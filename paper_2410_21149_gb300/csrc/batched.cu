@@ -126,9 +126,20 @@ __device__ __forceinline__ unsigned long long cta_sum_b(unsigned long long v, un
 template <bool kColour>
 __device__ void merge_part(const BatchDev& b, int s, int part, const MergeSmem& ms, unsigned long long* red) {
   const SubmapDev& m = b.views[b.meta[s].view];
-  const int nb = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
-  const bool skip = *((volatile int32_t*)m.frame_err) != 0;
-  const uint32_t ep = *((volatile uint32_t*)&m.st->epoch) + 1u + b.scans[s].epoch_add;
+  // Thread 0 reads the block count, error bits and epoch once for the CTA:
+  // the count grows while later scans' tiles allocate, and every thread must
+  // run the same spans (each merge_span holds CTA barriers).
+  __shared__ int head[3];
+  if (threadIdx.x == 0) {
+    head[0] = min(*((volatile int32_t*)&m.st->n_blocks), m.max_blocks);
+    head[1] = *((volatile int32_t*)m.frame_err);
+    head[2] = (int)(*((volatile uint32_t*)&m.st->epoch) + 1u + b.scans[s].epoch_add);
+  }
+  __syncthreads();
+  const int nb = head[0];
+  const bool skip = head[1] != 0;
+  const uint32_t ep = (uint32_t)head[2];
+  __syncthreads();   // head is rewritten by the CTA's next merge item
   unsigned long long merged = 0, touched = 0;
   for (int span = part; span * kSpanBlocks < nb; span += kSpansPerCall * kMergeParts) {
     int t = 0;

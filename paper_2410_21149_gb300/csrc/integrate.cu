@@ -281,11 +281,18 @@ __global__ void __launch_bounds__(kTileThreads, 5) integrate_pipelined_kernel(Su
   }
   if (*((volatile int32_t*)&a.st->pending) == 0) return;   // uniform over the merging CTAs
   const SubmapDev prev = pick_set(a, b, par ^ 1);
-  // blocks this scan's tiles allocate meanwhile carry other epochs: any count read here will do
-  const int nb = min(*((volatile int32_t*)&a.st->n_blocks), a.max_blocks);
-  const bool skip = *((volatile int32_t*)prev.frame_err) != 0;
-  const uint32_t ep = *((volatile uint32_t*)&a.st->epoch);   // the previous scan's epoch
-  merge_set<(kVariant < 0)>(prev, nb, ep, skip, (int)blockIdx.x - sc.n_tiles, n_merge, merge_smem(smem), red);
+  // Blocks this scan's tiles allocate meanwhile carry other epochs, so any
+  // count read here will do -- but one count for the whole CTA, read by
+  // thread 0: every thread must run the same spans (CTA barriers inside).
+  __shared__ int head[3];
+  if (threadIdx.x == 0) {
+    head[0] = min(*((volatile int32_t*)&a.st->n_blocks), a.max_blocks);
+    head[1] = *((volatile int32_t*)prev.frame_err);
+    head[2] = (int)*((volatile uint32_t*)&a.st->epoch);   // the previous scan's epoch
+  }
+  __syncthreads();
+  merge_set<(kVariant < 0)>(prev, head[0], (uint32_t)head[2], head[1] != 0, (int)blockIdx.x - sc.n_tiles, n_merge,
+                            merge_smem(smem), red);
 }
 
 // One thread, after integrate_pipelined_kernel: close the frame it merged

@@ -684,41 +684,60 @@ __global__ void __launch_bounds__(kFtW * kFtH, 3) point_weights_kernel(const flo
 // does not depend on scheduling), then every target divided by the mean.
 constexpr int kNormCtas = 256;
 
+// Compensated FP32 sum (Neumaier): s + c carries the exact sum to about one
+// rounding of its value, so the mean needs no FP64.
+struct CSum {
+  float s, c;
+};
+
+__device__ __forceinline__ void csum_add(CSum& a, float x) {
+  const float t = a.s + x;
+  a.c += fabsf(a.s) >= fabsf(x) ? (a.s - t) + x : (x - t) + a.s;
+  a.s = t;
+}
+
+__device__ __forceinline__ void csum_merge(CSum& a, const CSum& b) {
+  csum_add(a, b.s);
+  a.c += b.c;
+}
+
 __global__ void __launch_bounds__(256) target_sums_kernel(const float* __restrict__ e2,
                                                           const float* __restrict__ mask, long long n,
-                                                          double* __restrict__ partial) {
-  __shared__ double se[256], sm[256];
-  double a = 0.0, c = 0.0;
+                                                          float4* __restrict__ partial) {
+  __shared__ CSum se[256], sm[256];
+  CSum a{0.0f, 0.0f}, c{0.0f, 0.0f};
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
-    a += (double)e2[i] * (double)mask[i];
-    c += (double)mask[i];
+    const float mk = mask[i];
+    if (mk != 0.0f) {
+      csum_add(a, e2[i] * mk);
+      csum_add(c, mk);
+    }
   }
   se[threadIdx.x] = a;
   sm[threadIdx.x] = c;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) {
-      se[threadIdx.x] += se[threadIdx.x + o];
-      sm[threadIdx.x] += sm[threadIdx.x + o];
+      csum_merge(se[threadIdx.x], se[threadIdx.x + o]);
+      csum_merge(sm[threadIdx.x], sm[threadIdx.x + o]);
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = se[0];
-    partial[2 * blockIdx.x + 1] = sm[0];
-  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = make_float4(se[0].s, se[0].c, sm[0].s, sm[0].c);
 }
 
-__global__ void target_scale_kernel(float* __restrict__ e2, long long n, const double* __restrict__ partial,
+__global__ void target_scale_kernel(float* __restrict__ e2, long long n, const float4* __restrict__ partial,
                                     int nparts, float* __restrict__ mean_out) {
   __shared__ float inv;
   if (threadIdx.x == 0) {
-    double a = 0.0, c = 0.0;
+    CSum a{0.0f, 0.0f}, c{0.0f, 0.0f};
     for (int p = 0; p < nparts; ++p) {
-      a += partial[2 * p];
-      c += partial[2 * p + 1];
+      const float4 q = partial[p];
+      csum_merge(a, CSum{q.x, q.y});
+      csum_merge(c, CSum{q.z, q.w});
     }
-    const float mean = (float)(a / (c > 1.0 ? c : 1.0));
+    const float cnt = c.s + c.c;
+    const float mean = (a.s + a.c) / (cnt > 1.0f ? cnt : 1.0f);
     if (blockIdx.x == 0) *mean_out = mean;
     inv = mean > 0.0f ? 1.0f / mean : 1.0f;
   }
@@ -894,14 +913,14 @@ cvx_status cvx_weight_model_last(cvx_weight_model* w, float* grad, float* loss, 
 cvx_status cvx_normalise_targets(float* e2, const float* mask, int64_t n, float* mean_out, void* stream) {
   if (!e2 || !mask || !mean_out || n <= 0) return CVX_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  double* partial = nullptr;
+  float4* partial = nullptr;
   float* mean_dev = nullptr;
   // a small scratch of partials: stream-ordered allocation, freed on the stream
-  if (cudaMallocAsync((void**)&partial, sizeof(double) * 2 * kNormCtas + 16, s) != cudaSuccess) {
+  if (cudaMallocAsync((void**)&partial, sizeof(float4) * kNormCtas + 16, s) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_OOM;
   }
-  mean_dev = (float*)(partial + 2 * kNormCtas);
+  mean_dev = (float*)(partial + kNormCtas);
   COVOX_LAUNCH(kKTargets, s, target_sums_kernel<<<kNormCtas, 256, 0, s>>>(e2, mask, n, partial));
   const int grid = (int)std::min<long long>((n + 255) / 256, (long long)num_sms() * 8);
   COVOX_LAUNCH(kKTargets, s, target_scale_kernel<<<grid, 256, 0, s>>>(e2, n, partial, kNormCtas, mean_dev));
