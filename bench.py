@@ -32,20 +32,20 @@ import numpy as np  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 KERNEL_SOURCES = ("paper_2410_21149_gb300/csrc/covox_dev.cuh", "paper_2410_21149_gb300/csrc/integrate_dev.cuh",
-                  "paper_2410_21149_gb300/csrc/integrate.cu")
+                  "paper_2410_21149_gb300/csrc/integrate.cu", "paper_2410_21149_gb300/csrc/batched.cu")
 
 
-def kernel_traffic(name: str, ppc: int = 0, lb: int = 0):
-    """DRAM bytes per launch from the committed ncu summary for this kernel
-    and launch shape, or None if there is none or the kernel sources changed
-    since it was captured."""
+def kernel_traffic(name: str, ppc: int = 0, lb: int = 0, workload: str = ""):
+    """DRAM bytes per launch from the committed ncu summary for this kernel,
+    workload and launch shape, or None if there is none or the kernel sources
+    changed since it was captured."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    name = f"{name}|{ppc},{lb}" if f"{name}|{ppc},{lb}" in t else name
+    name = f"{name}|{workload}|{ppc},{lb}"
     if name not in t:
         return None
     h = hashlib.sha256()
@@ -572,7 +572,7 @@ def run_ours(args):
                                                   "pipelined": ps_pipe},
                                     "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof_ps.items() if v[1]}}},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": kernel_traffic(dom, args.ppc, args.lb), "peak_source": peak_src,
+                     "frac": achieved / hbm, "traffic": kernel_traffic(dom, args.ppc, args.lb, wl.name), "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms},
         "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / hbm,
                           "block_granular_bytes_per_step": 2 * S32 * 512 * blocks},
@@ -823,7 +823,10 @@ def lidar_numbers(args, ws, peaks, peak_src, storage=0, n_scans=2000):
                           "ms_per_step": r["ms_per_step_per_scan_path"],
                           "batched_speedup": r["ms_per_step_per_scan_path"] / r["ms_per_step"]},
         "roofline": {"bound": "hbm", "kernel": "batched_kernel", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                     "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
+                     "frac": ach / hbm,
+                     "traffic": kernel_traffic("batched_kernel", r["tuned"]["pts_per_cta"], r["tuned"]["local_blocks"],
+                                               wl.name) if storage == 0 else None,
+                     "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": r["kernel_bytes"], "avg_launch_ms": r["batched_kernel_ms"]},
         "counts_per_step": {k: r[k] for k in ("points", "observations", "voxels_merged", "blocks_touched",
                                               "blocks_allocated", "input_points")},
@@ -1099,6 +1102,47 @@ def run_reference(args):
     }), flush=True)
 
 
+def profile_steps(args):
+    """The benchmark's batched step, eagerly, args.profile_steps times: one
+    reset of every submap and one batched launch each, for a profiler to
+    capture (a small case: few frames or scans).  Launch shape --ppc/--lb, else
+    the shape the autotuner picks on GB300 (multiroom 1024 points per tile,
+    LiDAR 2048, both with L2 reductions)."""
+    import torch
+    import scenegen as sg
+    import paper_2410_21149_gb300 as cvx
+    from paper_2410_21149_gb300 import _capi
+    torch.cuda.set_device(0)
+    if args.workload == "lidar":
+        wl, max_blocks, ppc = sg.make_c3(n_scans=args.scans), 1 << 14, 2048
+    else:
+        wl, max_blocks, ppc = make_workload(args.workload, args.frames), 1 << 16, 1024
+    ppc, lb = (args.ppc, args.lb) if args.ppc else (ppc, -1)
+    subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, 0, max_blocks=max_blocks, sets=4)
+            for sm in wl.submaps]
+    scans, keep = [], []
+    for m, sm in enumerate(wl.submaps):
+        for sc in sm.scans:
+            p = torch.from_numpy(np.ascontiguousarray(sc.points)).cuda()
+            keep.append(p)
+            scans.append((m, p, sc.T_sub_sensor, None,
+                          cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range, sc.sensor,
+                                               sc.height, sc.width, ppc, lb)))
+    handles = [s.handle for s in subs]
+    batch = _capi.cvx_batch_create(len(subs), len(scans))
+    for _ in range(args.profile_steps):
+        _capi.cvx_reset_submaps(handles)
+        _capi.cvx_integrate_batch(batch, handles, scans)
+    torch.cuda.synchronize()
+    assert _capi.cvx_batch_error(batch) == 0 and all(s.status() == 0 for s in subs)
+    c = [s.counters() for s in subs]
+    print(json.dumps({"profile_steps": args.profile_steps, "workload": wl.name, "submaps": len(subs),
+                      "scans": len(scans), "launch_shape": [ppc, lb],
+                      "input_points": sum(int(x[1].shape[0]) for x in scans),
+                      "counts": {k: sum(x[k] for x in c) for k in c[0]}}))
+    _capi.cvx_batch_destroy(batch)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1122,7 +1166,12 @@ def main():
     ap.add_argument("--max-blocks", type=int, default=1 << 18)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiler mode: run only the batched step of --workload this many times, eagerly "
+                         "(--frames frames, or --scans LiDAR scans), no timing and no other forms")
     args = ap.parse_args()
+    if args.profile_steps > 0:
+        return profile_steps(args)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
