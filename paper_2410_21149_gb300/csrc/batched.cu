@@ -6,8 +6,8 @@
 // with no grid-wide barrier:
 //   tile item   one tile of one scan: integrate_tile (count, allocate,
 //               per-voxel sums; Sec. III-D) into the scan's per-scan set;
-//   merge item  one of kMergeParts parts of a scan's merge: every
-//               kMergeParts-th span of the submap's allocated blocks, the
+//   merge item  one of merge_parts parts of a scan's merge: every
+//               merge_parts-th span of the submap's allocated blocks, the
 //               blocks stamped with the scan's epoch merged into D and W.
 // An item waits (bounded) only for what it needs: a tile for the merge that
 // last used its per-scan set (pipelined submaps have two or four sets, so a
@@ -39,7 +39,7 @@ using namespace covox;
 
 namespace {
 
-constexpr int kMergeParts = 32;                  // merge items per scan
+constexpr int kMaxMergeParts = 256;              // merge items per scan, at most
 constexpr long long kWaitPolls = 1ll << 21;      // about a second of polling at the sleep below
 constexpr int kMaxBatchMaps = 1024;
 constexpr int kErrIncomplete = 8;                // a scan was left unmerged (only after a timeout)
@@ -65,6 +65,7 @@ struct BatchDev {
   int* ctr;                 // head, err, exit count, scans closed, then per scan: tiles done, merge tickets, merged flag
   unsigned long long* phase_ns;   // [1 + 2 * n_scans]: launch start, per scan tiles done / merged
   long long polls;          // polls before a wait gives up
+  int merge_parts;          // merge items per scan
   int missing_cta;          // test hook: this CTA takes one item and leaves without doing it (-1: none)
 };
 
@@ -120,7 +121,7 @@ __device__ __forceinline__ unsigned long long cta_sum_b(unsigned long long v, un
   return t;
 }
 
-// Merge part `part` of scan s: spans part, part + kMergeParts, ... of the
+// Merge part `part` of scan s: spans part, part + merge_parts, ... of the
 // submap's allocated blocks (blocks the submap's next scan allocates
 // meanwhile carry other epochs, so any count read now covers this scan's).
 template <bool kColour>
@@ -141,9 +142,9 @@ __device__ void merge_part(const BatchDev& b, int s, int part, const MergeSmem& 
   const uint32_t ep = (uint32_t)head[2];
   __syncthreads();   // head is rewritten by the CTA's next merge item
   unsigned long long merged = 0, touched = 0;
-  for (int span = part; span * kSpanBlocks < nb; span += kSpansPerCall * kMergeParts) {
+  for (int span = part; span * kSpanBlocks < nb; span += kSpansPerCall * b.merge_parts) {
     int t = 0;
-    merged += merge_span<kColour>(m, span, kMergeParts, nb, ep, skip, ms, &t);
+    merged += merge_span<kColour>(m, span, b.merge_parts, nb, ep, skip, ms, &t);
     touched += t;
   }
   const unsigned long long c = cta_sum_b(merged, red);
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) batched_kernel(BatchDev b) {
       merge_part<(kVariant < 0)>(b, s, part, merge_smem(smem), red);
       if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(merge_ticket(b, s), 1) == kMergeParts - 1) {
+        if (atomicAdd(merge_ticket(b, s), 1) == b.merge_parts - 1) {
           close_scan(b, s);
           if (b.phase_ns) b.phase_ns[2 + 2 * s] = global_ns();
           __threadfence();
@@ -263,6 +264,7 @@ struct cvx_batch {
   int wave_limit;     // most scans per round of the queue (0: no limit)
   int missing_cta;    // test hook (-1: off)
   long long polls;
+  int merge_parts;    // merge items per scan (0: chosen per launch)
 };
 
 namespace {
@@ -347,6 +349,12 @@ void cvx_batch_destroy(cvx_batch* b) {
 cvx_status cvx_batch_wave_limit(cvx_batch* b, int32_t max_scans_per_wave) {
   if (!b || max_scans_per_wave < 0) return CVX_ERR_INVALID_ARG;
   b->wave_limit = max_scans_per_wave;
+  return CVX_OK;
+}
+
+cvx_status cvx_batch_merge_parts(cvx_batch* b, int32_t parts) {
+  if (!b || parts < 0 || parts > kMaxMergeParts) return CVX_ERR_INVALID_ARG;
+  b->merge_parts = parts;
   return CVX_OK;
 }
 
@@ -469,6 +477,11 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     mt.epoch_end = rank[s] == per_map[q] - 1 ? per_map[q] : 0;
     prior.push_back(k);
   }
+  // Merge items per scan: a launch over few submaps is a few long chains of
+  // merges in frame order, so each merge is cut into many parts (short
+  // latency); over many submaps the chains run side by side and fewer,
+  // larger parts cost less queue traffic.
+  const int merge_parts = b->merge_parts > 0 ? b->merge_parts : (n_maps <= 4 ? 64 : (n_maps <= 16 ? 32 : 16));
   // queue segments, round by round: merges of the previous round's
   // single-set scans (their submaps' next tiles wait for them), this round's
   // tiles, then the merges of the previous round's two-set scans (the next
@@ -487,10 +500,10 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
       int k1 = k0;
       while (k1 < n_run && round_of[k1] == r) ++k1;
       for (int k = pk0; k < pk1; ++k)
-        if (!maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), kMergeParts);
+        if (!maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), merge_parts);
       for (int k = k0; k < k1; ++k) add_seg(k, hm[k].n_tiles);
       for (int k = pk0; k < pk1; ++k)
-        if (maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), kMergeParts);
+        if (maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), merge_parts);
       pk0 = k0;
       pk1 = k1;
       k0 = k1;
@@ -529,6 +542,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   bd.ctr = b->ctr;
   bd.phase_ns = b->timing ? b->phase_ns : nullptr;
   bd.polls = b->polls;
+  bd.merge_parts = merge_parts;
   bd.missing_cta = b->missing_cta;
   b->last_scans = n_run;
   // one variant for every scan: a kernel holding only that code
