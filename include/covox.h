@@ -345,7 +345,7 @@ cvx_status cvx_batch_wave_limit(cvx_batch* batch, int32_t max_scans_per_wave);
 
 /* Tuning: each scan's merge runs as `parts` work items of the persistent
  * launch (1..256; 0 = chosen per launch: 64 over at most 4 submaps, 32 over
- * at most 16, else 16).  Few submaps are few long chains of merges in frame
+ * at most 16, else 8).  Few submaps are few long chains of merges in frame
  * order, where more parts shorten each merge; many submaps run their chains
  * side by side, where fewer parts cost less queue traffic (Sec. III-D
  * workload equalisation).  Results do not depend on it. */

@@ -414,7 +414,7 @@ def cvx_profile_stop() -> None:
 
 def cvx_profile_read() -> dict:
     """{kernel name: (total ms, timed launches)} since the last read (synchronises)."""
-    k = 16
+    k = 32   # at least the library's number of kernel kinds
     names = ctypes.create_string_buffer(32 * k)
     tot = np.zeros(k, np.float64)
     cnt = np.zeros(k, np.int64)

@@ -177,8 +177,13 @@ __device__ __forceinline__ int find_segment(const BatchDev& b, int it) {
   return lo;
 }
 
+// Resident CTAs per SM the register budget is cut for (a build-time knob).
+#ifndef COVOX_BATCHED_MIN_CTAS
+#define COVOX_BATCHED_MIN_CTAS 4
+#endif
+
 template <int kVariant>
-__global__ void __launch_bounds__(kTileThreads, 3) batched_kernel(BatchDev b) {
+__global__ void __launch_bounds__(kTileThreads, COVOX_BATCHED_MIN_CTAS) batched_kernel(BatchDev b) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int item_smem[3];
   __shared__ int ok_smem;
@@ -481,7 +486,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   // merges in frame order, so each merge is cut into many parts (short
   // latency); over many submaps the chains run side by side and fewer,
   // larger parts cost less queue traffic.
-  const int merge_parts = b->merge_parts > 0 ? b->merge_parts : (n_maps <= 4 ? 64 : (n_maps <= 16 ? 32 : 16));
+  const int merge_parts = b->merge_parts > 0 ? b->merge_parts : (n_maps <= 4 ? 64 : (n_maps <= 16 ? 32 : 8));
   // queue segments, round by round: merges of the previous round's
   // single-set scans (their submaps' next tiles wait for them), this round's
   // tiles, then the merges of the previous round's two-set scans (the next

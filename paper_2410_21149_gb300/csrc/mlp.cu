@@ -48,49 +48,107 @@ __device__ __forceinline__ bool pt_valid(const float* P, int sensor) {
   return isfinite(P[0]) && isfinite(P[1]) && isfinite(P[2]) && (sensor != 0 || P[2] > 0.0f);
 }
 
-// One CTA per 32 x 8 pixel tile; the tile and its 2-pixel halo (36 x 12
-// points) are staged in shared memory once, with each point's validity and
-// depth (z for a pinhole, range for a spherical sensor).
-constexpr int kFtW = 32, kFtH = 8, kHalo = 2;
+// One CTA per 32 x 32 pixel tile, eight warps of four pixel rows each (warp
+// w takes rows 4w .. 4w + 3, lane = column); the tile and its 2-pixel halo
+// (36 x 36 points) are staged in shared memory once: each point's
+// coordinates, and its depth (z for a pinhole, range for a spherical sensor)
+// beside a validity weight of 1 or 0.
+constexpr int kFtW = 32, kFtH = 32, kHalo = 2, kFtRows = 4;
 constexpr int kFsW = kFtW + 2 * kHalo, kFsH = kFtH + 2 * kHalo;
+constexpr int kFtThreads = kFtW * kFtH / kFtRows;   // 256
+constexpr int kStageIters = (kFsW * kFsH + kFtThreads - 1) / kFtThreads;
 
-// The tile of a CTA and its 2-pixel halo in shared memory: points, validity
-// and depth (z for a pinhole, range for a spherical sensor).
 struct FeatTile {
   float sp[kFsH][kFsW][3];
-  float sz[kFsH][kFsW];
-  unsigned char sv[kFsH][kFsW];
+  float2 zm[kFsH][kFsW];   // (depth, 1) for a valid point, (0, 0) otherwise
 };
 
 __device__ __forceinline__ void stage_tile(FeatTile& T, const float* __restrict__ pts, int H, int W, int sensor,
                                            int x0, int y0) {
-  for (int q = threadIdx.x; q < kFsW * kFsH; q += blockDim.x) {
-    const int ly = q / kFsW, lx = q % kFsW, gx = x0 + lx, gy = y0 + ly;
-    float P0 = NAN, P1 = NAN, P2 = NAN;
-    if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-      const float* P = pts + 3 * ((size_t)gy * W + gx);
-      P0 = P[0]; P1 = P[1]; P2 = P[2];
+  // all loads of the thread first (independent), then the stores
+  float P[kStageIters][3];
+#pragma unroll
+  for (int j = 0; j < kStageIters; ++j) {
+    const int q = threadIdx.x + j * kFtThreads;
+    const int ly = q / kFsW, lx = q - ly * kFsW, gx = x0 + lx, gy = y0 + ly;
+    P[j][0] = P[j][1] = P[j][2] = NAN;
+    if (q < kFsW * kFsH && gx >= 0 && gx < W && gy >= 0 && gy < H) {
+      const float* src = pts + 3 * ((size_t)gy * W + gx);
+      P[j][0] = __ldg(src);
+      P[j][1] = __ldg(src + 1);
+      P[j][2] = __ldg(src + 2);
     }
-    const float Pv[3] = {P0, P1, P2};
-    const bool ok = pt_valid(Pv, sensor);
-    T.sp[ly][lx][0] = P0; T.sp[ly][lx][1] = P1; T.sp[ly][lx][2] = P2;
-    T.sv[ly][lx] = ok;
-    T.sz[ly][lx] = ok ? (sensor == 0 ? P2 : sqrtf(P0 * P0 + P1 * P1 + P2 * P2)) : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < kStageIters; ++j) {
+    const int q = threadIdx.x + j * kFtThreads;
+    if (q >= kFsW * kFsH) break;
+    const int ly = q / kFsW, lx = q - ly * kFsW;
+    const bool ok = pt_valid(P[j], sensor);
+    T.sp[ly][lx][0] = P[j][0];
+    T.sp[ly][lx][1] = P[j][1];
+    T.sp[ly][lx][2] = P[j][2];
+    const float z = sensor == 0 ? P[j][2] : sqrtf(P[j][0] * P[j][0] + P[j][1] * P[j][1] + P[j][2] * P[j][2]);
+    T.zm[ly][lx] = ok ? make_float2(z, 1.0f) : make_float2(0.0f, 0.0f);
   }
 }
 
-// Features of the point at tile position (tx, ty), image pixel (u, v).
-__device__ __forceinline__ void point_features(const FeatTile& T, int tx, int ty, int u, int v, int H, int W,
-                                               float max_range, float f[3]) {
-  const int cx = tx + kHalo, cy = ty + kHalo;
+// Third feature of the thread's four points (rows 4 ty + k of the tile,
+// column tx): ln(var + 1e-8) / 10 of the depths in the point's 5 x 5 window.
+// The variance of each window is taken about the point's own depth zc: with
+// s1 = sum (z - zc) and s2 = sum (z - zc)^2 over the window's valid points,
+// var = (s2 - s1^2 / n) / n -- the variance of the definition, whose
+// cancellation is bounded (zc is one of the window's points) -- and the
+// thread's four windows share their loads.
+__device__ __forceinline__ void tile_variance_features(const FeatTile& T, int tx, int ty, float f2[kFtRows]) {
+  float zc[kFtRows], s1[kFtRows], s2[kFtRows], cnt[kFtRows];
+#pragma unroll
+  for (int k = 0; k < kFtRows; ++k) {
+    zc[k] = T.zm[kFtRows * ty + k + kHalo][tx + kHalo].x;
+    s1[k] = s2[k] = cnt[k] = 0.0f;
+  }
+#pragma unroll
+  for (int dx = 0; dx < 2 * kHalo + 1; ++dx) {
+    float2 c[kFtRows + 2 * kHalo];
+#pragma unroll
+    for (int r = 0; r < kFtRows + 2 * kHalo; ++r) c[r] = T.zm[kFtRows * ty + r][tx + dx];
+#pragma unroll
+    for (int k = 0; k < kFtRows; ++k)
+#pragma unroll
+      for (int r = k; r <= k + 2 * kHalo; ++r) {
+        const float d = c[r].x - zc[k];
+        const float dm = d * c[r].y;   // 0 for an invalid point
+        s1[k] += dm;
+        s2[k] = fmaf(dm, d, s2[k]);
+        cnt[k] += c[r].y;
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < kFtRows; ++k) {
+    float var = 0.0f;
+    if (cnt[k] >= 3.0f) {
+      const float ic = __fdividef(1.0f, cnt[k]);
+      var = fmaxf((s2[k] - s1[k] * s1[k] * ic) * ic, 0.0f);
+    }
+    f2[k] = __logf(var + 1e-8f) * 0.1f;   // absolute error ~1e-7 over the feature's range
+  }
+}
+
+// Features of the point in row 4 ty + k, column tx of the tile (image pixel
+// (x0 + 2 + tx, y0 + 2 + 4 ty + k)), its third feature given: r / max_range,
+// the incidence angle / (pi / 2), and f2; all zero for an invalid point.
+__device__ __forceinline__ void point_features(const FeatTile& T, int tx, int ty, int k, int x0, int y0, int H, int W,
+                                               float inv_max_range, float f2, float f[3]) {
+  const int cx = tx + kHalo, cy = kFtRows * ty + k + kHalo;
+  const int u = x0 + cx, v = y0 + cy;
   f[0] = f[1] = f[2] = 0.0f;
-  if (!T.sv[cy][cx]) return;
+  if (T.zm[cy][cx].y == 0.0f) return;
   const float* P = T.sp[cy][cx];
   const float r = sqrtf(P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
-  f[0] = r / max_range;
+  f[0] = r * inv_max_range;
   float th = 0.0f;
-  if (u > 0 && u < W - 1 && v > 0 && v < H - 1 && T.sv[cy][cx - 1] && T.sv[cy][cx + 1] && T.sv[cy - 1][cx] &&
-      T.sv[cy + 1][cx]) {
+  if (u > 0 && u < W - 1 && v > 0 && v < H - 1 && T.zm[cy][cx - 1].y != 0.0f && T.zm[cy][cx + 1].y != 0.0f &&
+      T.zm[cy - 1][cx].y != 0.0f && T.zm[cy + 1][cx].y != 0.0f) {
     const float* L = T.sp[cy][cx - 1];
     const float* R = T.sp[cy][cx + 1];
     const float* U = T.sp[cy - 1][cx];
@@ -98,55 +156,38 @@ __device__ __forceinline__ void point_features(const FeatTile& T, int tx, int ty
     const float a0 = R[0] - L[0], a1 = R[1] - L[1], a2 = R[2] - L[2];
     const float b0 = Dn[0] - U[0], b1 = Dn[1] - U[1], b2 = Dn[2] - U[2];
     const float n0 = a1 * b2 - a2 * b1, n1 = a2 * b0 - a0 * b2, n2 = a0 * b1 - a1 * b0;
-    const float nn = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
-    if (nn > 0.0f) th = acosf(fminf(fabsf(n0 * P[0] + n1 * P[1] + n2 * P[2]) / (nn * r), 1.0f));
+    const float nn2 = n0 * n0 + n1 * n1 + n2 * n2;
+    // cos = |n.P| / (|n| r); rsqrtf's relative error (a few 1e-7) moves the
+    // angle by well under 1e-3 even where acos is steep
+    if (nn2 > 0.0f) th = acosf(fminf(fabsf(n0 * P[0] + n1 * P[1] + n2 * P[2]) * rsqrtf(nn2) / r, 1.0f));
   }
-  f[1] = th / 1.57079632679489662f;
-  // 5x5 window (clipped at the image border: out-of-image points are invalid)
-  float sum = 0.0f;
-  int cnt = 0;
-#pragma unroll
-  for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-    for (int dx = -2; dx <= 2; ++dx)
-      if (T.sv[cy + dy][cx + dx]) {
-        sum += T.sz[cy + dy][cx + dx];
-        ++cnt;
-      }
-  float var = 0.0f;
-  if (cnt >= 3) {
-    const float mu = sum / cnt;
-    float ss = 0.0f;
-#pragma unroll
-    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-      for (int dx = -2; dx <= 2; ++dx)
-        if (T.sv[cy + dy][cx + dx]) {
-          const float e = T.sz[cy + dy][cx + dx] - mu;
-          ss += e * e;
-        }
-    var = ss / cnt;
-  }
-  f[2] = logf(var + 1e-8f) / 10.0f;
+  f[1] = th * 0.636619772367581343f;   // / (pi / 2)
+  f[2] = f2;
 }
 
-__global__ void __launch_bounds__(kFtW * kFtH) features_kernel(const float* __restrict__ pts, int H, int W,
-                                                                 int sensor, float max_range,
-                                                                 float* __restrict__ out) {
+__global__ void __launch_bounds__(kFtThreads) features_kernel(const float* __restrict__ pts, int H, int W,
+                                                               int sensor, float max_range,
+                                                               float* __restrict__ out) {
   __shared__ FeatTile T;
   const int tiles_x = (W + kFtW - 1) / kFtW;
   const int x0 = (blockIdx.x % tiles_x) * kFtW - kHalo, y0 = (blockIdx.x / tiles_x) * kFtH - kHalo;
   stage_tile(T, pts, H, W, sensor, x0, y0);
   __syncthreads();
-  const int tx = threadIdx.x % kFtW, ty = threadIdx.x / kFtW;
-  const int u = x0 + kHalo + tx, v = y0 + kHalo + ty;
-  if (u >= W || v >= H) return;
-  float f[3];
-  point_features(T, tx, ty, u, v, H, W, max_range, f);
-  const size_t idx = (size_t)v * W + u;
-  out[3 * idx] = f[0];
-  out[3 * idx + 1] = f[1];
-  out[3 * idx + 2] = f[2];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float f2[kFtRows];
+  tile_variance_features(T, tx, ty, f2);
+  const int u = x0 + kHalo + tx;
+#pragma unroll
+  for (int k = 0; k < kFtRows; ++k) {
+    const int v = y0 + kHalo + kFtRows * ty + k;
+    if (u >= W || v >= H) continue;
+    float f[3];
+    point_features(T, tx, ty, k, x0, y0, H, W, 1.0f / max_range, f2[k], f);
+    const size_t idx = (size_t)v * W + u;
+    out[3 * idx] = f[0];
+    out[3 * idx + 1] = f[1];
+    out[3 * idx + 2] = f[2];
+  }
 }
 
 // ------------------------------------------------------- training targets
@@ -523,17 +564,19 @@ __global__ void __launch_bounds__(32 * kIWarps) mlp_infer_kernel(const float* __
 }
 
 // ------------------------------------------------ fused features + network
-// Per-point weights of an organised scan in one pass: each CTA stages a
-// 32 x 8 pixel tile (and halo) in shared memory, every thread computes its
-// point's features, and each warp (one row of 32 pixels, two 16-point row
-// blocks) runs the network on the tensor cores with mma.sync m16n8k16 BF16
-// fragments that stay in registers from layer to layer: the FP32 accumulator
-// layout of a 16 x 8 output tile, two tiles side by side, is the A-operand
-// layout of the next layer's 16-wide K slice, so ReLU, bias and the BF16
-// rounding are applied in place.  The output layer (32 -> 1) is a dot product
-// of each lane's eight BF16 activations per row with W3, summed over the four
-// lanes of a row.  Same roundings as mlp_infer_kernel: BF16 operands of both
-// GEMMs, FP32 accumulation, W3 and the biases in FP32.
+// Per-point weights of organised scans in one pass: each CTA stages a 32 x 32
+// pixel tile (and halo) in shared memory, every thread computes the features
+// of its four points (one per pixel row it owns), and each warp runs the
+// network on one row of 32 points at a time (two 16-point row blocks) with
+// mma.sync m16n8k16 BF16 fragments that stay in registers from layer to
+// layer: the FP32 accumulator layout of a 16 x 8 output tile, two tiles side
+// by side, is the A-operand layout of the next layer's 16-wide K slice.  Each
+// accumulator starts at its layer's bias, and one cvt.rn.relu.bf16x2 applies
+// ReLU and the BF16 rounding to two activations at once.  The output layer
+// (32 -> 1) is a third GEMM whose two B columns hold W3 as a pair of BF16
+// values, hi = bf16(W3) and lo = bf16(W3 - hi) (16 significant bits; the
+// products are exact and accumulate in FP32), so o = b3 + hi.h + lo.h.
+// Roundings: BF16 operands of every GEMM, FP32 accumulation, biases in FP32.
 __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -542,24 +585,134 @@ __device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// d = a b + c with the accumulator input c apart from the output d (a bias
+// broadcast to both rows needs no copies).
+__device__ __forceinline__ void mma_bf16_16816_c(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1, float c0,
+                                                 float c1, float c2, float c3) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%11,%12,%13};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2), "f"(c3));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// (bf16(max(lo, 0)), bf16(max(hi, 0))) packed low / high, round to nearest even.
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
 struct WeightParamsSmem {
   float w1[kH * kIn], b1[kH], w2[kH * kH], b2[kH], w3[kH], b3;
 };
 
+// Per-lane operands of the three GEMMs in mma.sync fragment layout
+// (B[k][n] = W[n][k], col-major K x N), held in registers across items.
+struct WeightFrags {
+  uint32_t b1[4];       // layer 1, n-tiles 0..3
+  uint32_t b2[4][4];    // layer 2, n-tile nt: (kt 0: b0, b1), (kt 1: b0, b1)
+  uint32_t b3[4];       // layer 3: (kt 0: b0, b1), (kt 1: b0, b1)
+  float2 bias1[4];      // this lane's two accumulator columns of each n-tile: b1
+  float2 bias2[4];      //   and b2
+};
+
+__device__ __forceinline__ void build_fragments(const WeightParamsSmem& S, WeightFrags& F, int lane) {
+  const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int n = nt * 8 + g;
+    const int k0 = tig * 2;
+    F.b1[nt] = pack_bf16(k0 < kIn ? S.w1[n * kIn + k0] : 0.0f, k0 + 1 < kIn ? S.w1[n * kIn + k0 + 1] : 0.0f);
+#pragma unroll
+    for (int kt = 0; kt < 2; ++kt) {
+      const int k = kt * 16 + tig * 2;
+      F.b2[nt][2 * kt] = pack_bf16(S.w2[n * kH + k], S.w2[n * kH + k + 1]);
+      F.b2[nt][2 * kt + 1] = pack_bf16(S.w2[n * kH + k + 8], S.w2[n * kH + k + 9]);
+    }
+    F.bias1[nt] = make_float2(S.b1[nt * 8 + tig * 2], S.b1[nt * 8 + tig * 2 + 1]);
+    F.bias2[nt] = make_float2(S.b2[nt * 8 + tig * 2], S.b2[nt * 8 + tig * 2 + 1]);
+  }
+  // output layer: column 0 of B holds bf16(W3), column 1 the BF16 remainder
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float w3 = S.w3[kt * 16 + h * 8 + tig * 2 + j];
+        const float hi = __bfloat162float(__float2bfloat16_rn(w3));
+        v[j] = g == 0 ? hi : (g == 1 ? w3 - hi : 0.0f);
+      }
+      F.b3[2 * kt + h] = pack_bf16(v[0], v[1]);
+    }
+}
+
+// Network output o (before the softplus) of 16 points, rows g and g + 8 of a
+// row block: layer-1 A fragments A0 (row g) and A1 (row g + 8) hold the
+// features (K padded to 16).  Lanes with tig == 0 receive o of rows g (og)
+// and g + 8 (og8).
+__device__ __forceinline__ void network_rows(const WeightFrags& F, int lane, uint32_t A0, uint32_t A1, float b3,
+                                             float& og, float& og8) {
+  const int tig = lane & 3;
+  const uint32_t A[4] = {A0, A1, 0u, 0u};
+  // layer 1: C = b1 + x W1^T
+  float C[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+    mma_bf16_16816_c(C[nt], A, F.b1[nt], 0u, F.bias1[nt].x, F.bias1[nt].y, F.bias1[nt].x, F.bias1[nt].y);
+  // h1 = bf16(relu(C)) in the A layout of layer 2: {row g, k..k+1},
+  // {row g+8, k..}, {row g, k+8..}, {row g+8, k+8..} of each K slice
+  uint32_t A2[2][4];
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      A2[kt][2 * h] = pack_relu_bf16(C[2 * kt + h][0], C[2 * kt + h][1]);
+      A2[kt][2 * h + 1] = pack_relu_bf16(C[2 * kt + h][2], C[2 * kt + h][3]);
+    }
+  // layer 2: D = b2 + h1 W2^T
+  float D[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    mma_bf16_16816_c(D[nt], A2[0], F.b2[nt][0], F.b2[nt][1], F.bias2[nt].x, F.bias2[nt].y, F.bias2[nt].x,
+                     F.bias2[nt].y);
+    mma_bf16_16816(D[nt], A2[1], F.b2[nt][2], F.b2[nt][3]);
+  }
+  uint32_t A3[2][4];
+#pragma unroll
+  for (int kt = 0; kt < 2; ++kt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      A3[kt][2 * h] = pack_relu_bf16(D[2 * kt + h][0], D[2 * kt + h][1]);
+      A3[kt][2 * h + 1] = pack_relu_bf16(D[2 * kt + h][2], D[2 * kt + h][3]);
+    }
+  // layer 3: E[., 0] = b3 + bf16(W3) h2, E[., 1] = remainder(W3) h2
+  const float e0 = tig == 0 ? b3 : 0.0f;
+  float E[4];
+  mma_bf16_16816_c(E, A3[0], F.b3[0], F.b3[1], e0, 0.0f, e0, 0.0f);
+  mma_bf16_16816(E, A3[1], F.b3[2], F.b3[3]);
+  og = E[0] + E[1];
+  og8 = E[2] + E[3];
+}
+
+// Resident CTAs per SM the register budget of point_weights_kernel is cut
+// for (a build-time knob).
+#ifndef COVOX_PW_MIN_CTAS
+#define COVOX_PW_MIN_CTAS 2
+#endif
+
 // Features and network of n_frames organised scans [n_frames, H, W, 3] in one
-// persistent launch: CTAs take (frame, 32 x 8 tile) items in frame-major
-// order.  The weight fragments stay in registers across items; the biases and
-// output weights are read from shared memory (broadcast), which keeps three
-// 256-thread CTAs resident per SM.
-__global__ void __launch_bounds__(kFtW * kFtH, 3) point_weights_kernel(const float* __restrict__ params,
-                                                                         const float* __restrict__ pts, int n_frames,
-                                                                         int H, int W, int sensor, float max_range,
-                                                                         float* __restrict__ wout) {
+// persistent launch: CTAs take (frame, 32 x 32 tile) items in frame-major
+// order.  The GEMM operands stay in registers in fragment layout.
+__global__ void __launch_bounds__(kFtThreads, COVOX_PW_MIN_CTAS) point_weights_kernel(
+    const float* __restrict__ params, const float* __restrict__ pts, int n_frames, int H, int W, int sensor,
+    float max_range, float* __restrict__ wout) {
   __shared__ FeatTile T;
   __shared__ WeightParamsSmem S;
   for (int q = threadIdx.x; q < kP; q += blockDim.x) {
@@ -573,25 +726,14 @@ __global__ void __launch_bounds__(kFtW * kFtH, 3) point_weights_kernel(const flo
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
-  // B fragments (col-major K x N, B[k][n] = W[n][k]) of both layers, and the
-  // per-column biases / output weights this lane's accumulator columns see
-  uint32_t B1[4], B2[4][2][2];
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    const int n = nt * 8 + g;
-    const int k0 = tig * 2;
-    B1[nt] = pack_bf16(k0 < kIn ? S.w1[n * kIn + k0] : 0.0f, k0 + 1 < kIn ? S.w1[n * kIn + k0 + 1] : 0.0f);
-#pragma unroll
-    for (int kt = 0; kt < 2; ++kt) {
-      const int k = kt * 16 + tig * 2;
-      B2[nt][kt][0] = pack_bf16(S.w2[n * kH + k], S.w2[n * kH + k + 1]);
-      B2[nt][kt][1] = pack_bf16(S.w2[n * kH + k + 8], S.w2[n * kH + k + 9]);
-    }
-  }
+  WeightFrags F;
+  build_fragments(S, F, lane);
+  const float b3 = S.b3;
+  const float inv_max_range = 1.0f / max_range;
   const int tiles_x = (W + kFtW - 1) / kFtW;
   const int n_tiles = tiles_x * ((H + kFtH - 1) / kFtH);
   const long long n_items = (long long)n_tiles * n_frames;
-  const int tx = threadIdx.x % kFtW, ty = threadIdx.x / kFtW;
+  const int tx = lane, ty = threadIdx.x >> 5;
   for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int frame = (int)(item / n_tiles), tile = (int)(item % n_tiles);
     const float* fpts = pts + (size_t)frame * H * W * 3;
@@ -600,81 +742,34 @@ __global__ void __launch_bounds__(kFtW * kFtH, 3) point_weights_kernel(const flo
     __syncthreads();   // the previous tile's staging is no longer read
     stage_tile(T, fpts, H, W, sensor, x0, y0);
     __syncthreads();
-    const int u = x0 + kHalo + tx, v = y0 + kHalo + ty;
-    float f[3] = {0.0f, 0.0f, 0.0f};
-    if (u < W && v < H) point_features(T, tx, ty, u, v, H, W, max_range, f);
-    float wpt[2] = {0.0f, 0.0f};   // this lane's output rows g and g + 8 of each row block
+    float f2[kFtRows];
+    tile_variance_features(T, tx, ty, f2);
+#pragma unroll 1
+    for (int k = 0; k < kFtRows; ++k) {
+      float f[3];
+      point_features(T, tx, ty, k, x0, y0, H, W, inv_max_range, f2[k], f);
+      // network of this warp's row k: points (columns) 16 mt + g and 16 mt + g + 8
+      float og[2], og8[2];
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      // layer 1: A = features of points mt*16 + g and + 8 (K padded to 16)
-      const int pa = mt * 16 + g, pb = pa + 8;
-      const float fa0 = __shfl_sync(0xffffffffu, f[0], pa), fa1 = __shfl_sync(0xffffffffu, f[1], pa);
-      const float fa2 = __shfl_sync(0xffffffffu, f[2], pa);
-      const float fb0 = __shfl_sync(0xffffffffu, f[0], pb), fb1 = __shfl_sync(0xffffffffu, f[1], pb);
-      const float fb2 = __shfl_sync(0xffffffffu, f[2], pb);
-      uint32_t A[4];
-      A[0] = tig == 0 ? pack_bf16(fa0, fa1) : (tig == 1 ? pack_bf16(fa2, 0.0f) : 0u);
-      A[1] = tig == 0 ? pack_bf16(fb0, fb1) : (tig == 1 ? pack_bf16(fb2, 0.0f) : 0u);
-      A[2] = 0u;
-      A[3] = 0u;
-      float C[4][4];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        C[nt][0] = C[nt][1] = C[nt][2] = C[nt][3] = 0.0f;
-        mma_bf16_16816(C[nt], A, B1[nt], 0u);
+      for (int mt = 0; mt < 2; ++mt) {
+        const int pa = mt * 16 + g, pb = pa + 8;
+        const float fa0 = __shfl_sync(0xffffffffu, f[0], pa), fa1 = __shfl_sync(0xffffffffu, f[1], pa);
+        const float fa2 = __shfl_sync(0xffffffffu, f[2], pa);
+        const float fb0 = __shfl_sync(0xffffffffu, f[0], pb), fb1 = __shfl_sync(0xffffffffu, f[1], pb);
+        const float fb2 = __shfl_sync(0xffffffffu, f[2], pb);
+        const uint32_t A0 = tig == 0 ? pack_bf16(fa0, fa1) : (tig == 1 ? pack_bf16(fa2, 0.0f) : 0u);
+        const uint32_t A1 = tig == 0 ? pack_bf16(fb0, fb1) : (tig == 1 ? pack_bf16(fb2, 0.0f) : 0u);
+        network_rows(F, lane, A0, A1, b3, og[mt], og8[mt]);
       }
-      // h1 = relu(. + b1), rounded to BF16: the A operand of layer 2
-      uint32_t A2[2][4];
-#pragma unroll
-      for (int kt = 0; kt < 2; ++kt) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int nt = 2 * kt + h;
-          const float c0 = S.b1[nt * 8 + tig * 2], c1 = S.b1[nt * 8 + tig * 2 + 1];
-          A2[kt][2 * h] = pack_bf16(fmaxf(C[nt][0] + c0, 0.0f), fmaxf(C[nt][1] + c1, 0.0f));
-          A2[kt][2 * h + 1] = pack_bf16(fmaxf(C[nt][2] + c0, 0.0f), fmaxf(C[nt][3] + c1, 0.0f));
-        }
-      }
-      // the A layout wants {row g, cols k..k+1}, {row g+8, k..}, {row g, k+8..}, {row g+8, k+8..}
-      uint32_t A2r[2][4];
-#pragma unroll
-      for (int kt = 0; kt < 2; ++kt) {
-        A2r[kt][0] = A2[kt][0];
-        A2r[kt][1] = A2[kt][1];
-        A2r[kt][2] = A2[kt][2];
-        A2r[kt][3] = A2[kt][3];
-      }
-      // layer 2
-      float D[4][4];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        D[nt][0] = D[nt][1] = D[nt][2] = D[nt][3] = 0.0f;
-#pragma unroll
-        for (int kt = 0; kt < 2; ++kt) mma_bf16_16816(D[nt], A2r[kt], B2[nt][kt][0], B2[nt][kt][1]);
-      }
-      // output layer on BF16(relu(. + b2))
-      float oa = 0.0f, ob = 0.0f;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int col = nt * 8 + tig * 2 + j;
-          const float b2 = S.b2[col], w3 = S.w3[col];
-          oa += w3 * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][j] + b2, 0.0f)));
-          ob += w3 * __bfloat162float(__float2bfloat16_rn(fmaxf(D[nt][2 + j] + b2, 0.0f)));
-        }
-      oa += __shfl_xor_sync(0xffffffffu, oa, 1);
-      oa += __shfl_xor_sync(0xffffffffu, oa, 2);
-      ob += __shfl_xor_sync(0xffffffffu, ob, 1);
-      ob += __shfl_xor_sync(0xffffffffu, ob, 2);
-      wpt[mt] = tig == 0 ? softplus_f(oa + S.b3) : (tig == 1 ? softplus_f(ob + S.b3) : 0.0f);
-    }
-    // lane (g, tig) holds the weights of points mt*16 + g (tig 0) and + 8 (tig 1)
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int pt = mt * 16 + g + (tig == 1 ? 8 : 0);
-      const int gu = x0 + kHalo + pt;
-      if (tig < 2 && gu < W && v < H) fw[(size_t)v * W + gu] = wpt[mt];
+      // lane L takes the output of its own point (column L): row L & 15 of row
+      // block L >> 4, held by lane 4 (L & 7)
+      const int src = (lane & 7) * 4;
+      const float v00 = __shfl_sync(0xffffffffu, og[0], src), v01 = __shfl_sync(0xffffffffu, og8[0], src);
+      const float v10 = __shfl_sync(0xffffffffu, og[1], src), v11 = __shfl_sync(0xffffffffu, og8[1], src);
+      const bool lo8 = (lane & 8) == 0;
+      const float o = lane < 16 ? (lo8 ? v00 : v01) : (lo8 ? v10 : v11);
+      const int u = x0 + kHalo + tx, v = y0 + kHalo + kFtRows * ty + k;
+      if (u < W && v < H) fw[(size_t)v * W + u] = softplus_f(o);
     }
   }
 }
@@ -845,7 +940,7 @@ cvx_status cvx_point_features(const float* points, int32_t height, int32_t width
   cudaStream_t s = (cudaStream_t)stream;
   const int tiles = ((width + kFtW - 1) / kFtW) * ((height + kFtH - 1) / kFtH);
   COVOX_LAUNCH(kKFeatures, s,
-               features_kernel<<<tiles, kFtW * kFtH, 0, s>>>(points, height, width, sensor, max_range, features));
+               features_kernel<<<tiles, kFtThreads, 0, s>>>(points, height, width, sensor, max_range, features));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
 
@@ -869,9 +964,16 @@ cvx_status cvx_weight_model_point_weights_frames(cvx_weight_model* w, const floa
   if ((long long)n_frames * height * width > (1ll << 40)) return CVX_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const long long items = (long long)((width + kFtW - 1) / kFtW) * ((height + kFtH - 1) / kFtH) * n_frames;
-  const int grid = (int)std::min<long long>(items, (long long)num_sms() * 3);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)point_weights_kernel, kFtThreads, 0) !=
+          cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  const int grid = (int)std::min<long long>(items, (long long)num_sms() * per_sm);
   COVOX_LAUNCH(kKPointWeights, s,
-               point_weights_kernel<<<grid, kFtW * kFtH, 0, s>>>(w->params, points, n_frames, height, width, sensor,
+               point_weights_kernel<<<grid, kFtThreads, 0, s>>>(w->params, points, n_frames, height, width, sensor,
                                                                   max_range, weights));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
