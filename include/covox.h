@@ -344,11 +344,14 @@ cvx_status cvx_integrate_batch(cvx_batch* batch, cvx_submap* const* maps, int32_
 cvx_status cvx_batch_wave_limit(cvx_batch* batch, int32_t max_scans_per_wave);
 
 /* Tuning: each scan's merge runs as `parts` work items of the persistent
- * launch (1..256; 0 = chosen per launch: 64 over at most 4 submaps, 32 over
- * at most 16, else 8).  Few submaps are few long chains of merges in frame
- * order, where more parts shorten each merge; many submaps run their chains
- * side by side, where fewer parts cost less queue traffic (Sec. III-D
- * workload equalisation).  Results do not depend on it. */
+ * launch (1..256; 0 = chosen per round of the queue, a round being the scans
+ * of equal rank in their submaps: the largest power of two in [8, 64] whose
+ * product with the round's scan count stays within the launch's resident
+ * CTAs).  A round of few scans -- one submap, or the last frames of the
+ * longest chains -- is a few merges on the critical path, where more parts
+ * shorten each merge; many scans run their merges side by side, where fewer
+ * parts cost less queue traffic (Sec. III-D workload equalisation).  Results
+ * do not depend on it. */
 cvx_status cvx_batch_merge_parts(cvx_batch* batch, int32_t parts);
 
 /* CVX_ERR_TIMEOUT if a wait of the last batch gave up (synchronous). */

@@ -6,8 +6,8 @@
 // with no grid-wide barrier:
 //   tile item   one tile of one scan: integrate_tile (count, allocate,
 //               per-voxel sums; Sec. III-D) into the scan's per-scan set;
-//   merge item  one of merge_parts parts of a scan's merge: every
-//               merge_parts-th span of the submap's allocated blocks, the
+//   merge item  one of the scan's merge parts: every parts-th span of
+//               the submap's allocated blocks, the
 //               blocks stamped with the scan's epoch merged into D and W.
 // An item waits (bounded) only for what it needs: a tile for the merge that
 // last used its per-scan set (pipelined submaps have two or four sets, so a
@@ -52,6 +52,7 @@ struct ScanMeta {
   int n_tiles;
   int lb;         // shared block slots
   int epoch_end;  // > 0: the submap's last scan of the launch, st->epoch advances by this much
+  int parts;      // merge items of the scan
 };
 
 struct BatchDev {
@@ -65,7 +66,6 @@ struct BatchDev {
   int* ctr;                 // head, err, exit count, scans closed, then per scan: tiles done, merge tickets, merged flag
   unsigned long long* phase_ns;   // [1 + 2 * n_scans]: launch start, per scan tiles done / merged
   long long polls;          // polls before a wait gives up
-  int merge_parts;          // merge items per scan
   int missing_cta;          // test hook: this CTA takes one item and leaves without doing it (-1: none)
 };
 
@@ -121,7 +121,7 @@ __device__ __forceinline__ unsigned long long cta_sum_b(unsigned long long v, un
   return t;
 }
 
-// Merge part `part` of scan s: spans part, part + merge_parts, ... of the
+// Merge part `part` of scan s: spans part, part + parts, ... of the
 // submap's allocated blocks (blocks the submap's next scan allocates
 // meanwhile carry other epochs, so any count read now covers this scan's).
 template <bool kColour>
@@ -142,9 +142,10 @@ __device__ void merge_part(const BatchDev& b, int s, int part, const MergeSmem& 
   const uint32_t ep = (uint32_t)head[2];
   __syncthreads();   // head is rewritten by the CTA's next merge item
   unsigned long long merged = 0, touched = 0;
-  for (int span = part; span * kSpanBlocks < nb; span += kSpansPerCall * b.merge_parts) {
+  const int parts = b.meta[s].parts;
+  for (int span = part; span * kSpanBlocks < nb; span += kSpansPerCall * parts) {
     int t = 0;
-    merged += merge_span<kColour>(m, span, b.merge_parts, nb, ep, skip, ms, &t);
+    merged += merge_span<kColour>(m, span, parts, nb, ep, skip, ms, &t);
     touched += t;
   }
   const unsigned long long c = cta_sum_b(merged, red);
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kTileThreads, COVOX_BATCHED_MIN_CTAS) batched_
       merge_part<(kVariant < 0)>(b, s, part, merge_smem(smem), red);
       if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(merge_ticket(b, s), 1) == b.merge_parts - 1) {
+        if (atomicAdd(merge_ticket(b, s), 1) == sm.parts - 1) {
           close_scan(b, s);
           if (b.phase_ns) b.phase_ns[2 + 2 * s] = global_ns();
           __threadfence();
@@ -269,7 +270,7 @@ struct cvx_batch {
   int wave_limit;     // most scans per round of the queue (0: no limit)
   int missing_cta;    // test hook (-1: off)
   long long polls;
-  int merge_parts;    // merge items per scan (0: chosen per launch)
+  int merge_parts;    // merge items per scan (0: chosen per round of each launch)
 };
 
 namespace {
@@ -482,11 +483,36 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     mt.epoch_end = rank[s] == per_map[q] - 1 ? per_map[q] : 0;
     prior.push_back(k);
   }
-  // Merge items per scan: a launch over few submaps is a few long chains of
-  // merges in frame order, so each merge is cut into many parts (short
-  // latency); over many submaps the chains run side by side and fewer,
-  // larger parts cost less queue traffic.
-  const int merge_parts = b->merge_parts > 0 ? b->merge_parts : (n_maps <= 4 ? 64 : (n_maps <= 16 ? 32 : 8));
+  // one variant for every scan: a kernel holding only that code
+  int variant = -2;
+  for (int k = 0; k < n_run; ++k) {
+    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff, general_form(sd[order[k]]));
+    variant = variant == -2 ? v : (variant == v ? v : -1);
+  }
+  const BatchedFn kern = kBatched[variant + 1];
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kTileThreads,
+                                                    tile_smem_bytes(lb_max)) != cudaSuccess ||
+      per_sm <= 0) {
+    cudaGetLastError();
+    return CVX_ERR_CUDA;
+  }
+  const int ctas = per_sm * num_sms();
+  // Merge items per scan, per round of the queue: a round of few scans (one
+  // submap, or the last frames of the longest chains) is a few merges on the
+  // critical path, each cut into many parts (short latency); a round of many
+  // scans runs its merges side by side, where fewer, larger parts cost less
+  // queue traffic.  About one merge item per resident CTA per round: the
+  // largest power of two <= ctas / (scans of the round), within [8, 64].
+  std::vector<int> round_size(n_rounds, 0);
+  for (int k = 0; k < n_run; ++k) ++round_size[round_of[k]];
+  auto parts_of_round = [&](int r) {
+    if (b->merge_parts > 0) return b->merge_parts;
+    int p = 8;
+    while (p < 64 && 2 * p * round_size[r] <= ctas) p *= 2;
+    return p;
+  };
+  for (int k = 0; k < n_run; ++k) hm[k].parts = parts_of_round(round_of[k]);
   // queue segments, round by round: merges of the previous round's
   // single-set scans (their submaps' next tiles wait for them), this round's
   // tiles, then the merges of the previous round's two-set scans (the next
@@ -505,10 +531,10 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
       int k1 = k0;
       while (k1 < n_run && round_of[k1] == r) ++k1;
       for (int k = pk0; k < pk1; ++k)
-        if (!maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), merge_parts);
+        if (!maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), hm[k].parts);
       for (int k = k0; k < k1; ++k) add_seg(k, hm[k].n_tiles);
       for (int k = pk0; k < pk1; ++k)
-        if (maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), merge_parts);
+        if (maps[scans[order[k]].submap]->pipelined) add_seg(k | (1 << 30), hm[k].parts);
       pk0 = k0;
       pk1 = k1;
       k0 = k1;
@@ -547,24 +573,9 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   bd.ctr = b->ctr;
   bd.phase_ns = b->timing ? b->phase_ns : nullptr;
   bd.polls = b->polls;
-  bd.merge_parts = merge_parts;
   bd.missing_cta = b->missing_cta;
   b->last_scans = n_run;
-  // one variant for every scan: a kernel holding only that code
-  int variant = -2;
-  for (int k = 0; k < n_run; ++k) {
-    const int v = tile_variant(lbs[order[k]], sd[order[k]].dropoff, general_form(sd[order[k]]));
-    variant = variant == -2 ? v : (variant == v ? v : -1);
-  }
-  const BatchedFn kern = kBatched[variant + 1];
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kTileThreads,
-                                                    tile_smem_bytes(lb_max)) != cudaSuccess ||
-      per_sm <= 0) {
-    cudaGetLastError();
-    return CVX_ERR_CUDA;
-  }
-  const int grid = std::min(per_sm * num_sms(), std::max(items, 1));   // one wave of resident CTAs
+  const int grid = std::min(ctas, std::max(items, 1));   // one wave of resident CTAs
   COVOX_LAUNCH(kKBatched, st, kern<<<grid, kTileThreads, tile_smem_bytes(lb_max), st>>>(bd));
   return cudaGetLastError() == cudaSuccess ? CVX_OK : CVX_ERR_CUDA;
 }
