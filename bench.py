@@ -1113,33 +1113,51 @@ def profile_steps(args):
     import paper_2410_21149_gb300 as cvx
     from paper_2410_21149_gb300 import _capi
     torch.cuda.set_device(0)
+    if args.profile_kernel == "point_weights":
+        # the learned form's weight kernel over the frames, untrained network
+        from paper_2410_21149_gb300 import weights
+        wl = make_workload(args.workload if args.workload != "lidar" else "multiroom", args.frames)
+        sm = wl.submaps[0]
+        H, W = sm.scans[0].height, sm.scans[0].width
+        pts = torch.from_numpy(np.stack([sc.points for sc in sm.scans])).cuda()
+        model = weights.WeightModel(seed=0)
+        w = torch.empty((len(sm.scans), H * W), dtype=torch.float32, device="cuda")
+        for _ in range(args.profile_steps):
+            weights.learned_point_weights_frames(model, pts, H, W, sm.scans[0].sensor, wl.max_range, out=w)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(w).all())
+        print(json.dumps({"profile_steps": args.profile_steps, "kernel": "point_weights_kernel",
+                          "workload": wl.name, "frames": len(sm.scans), "points": int(pts.shape[0] * pts.shape[1])}))
+        model.close()
+        return
     if args.workload == "lidar":
         wl, max_blocks, ppc = sg.make_c3(n_scans=args.scans), 1 << 14, 2048
     else:
         wl, max_blocks, ppc = make_workload(args.workload, args.frames), 1 << 16, 1024
-    ppc, lb = (args.ppc, args.lb) if args.ppc else (ppc, -1)
+    if args.profile_shapes:   # "ppc,lb;ppc,lb;...": each shape's launches in turn, in this order
+        shapes = [tuple(int(v) for v in x.split(",")) for x in args.profile_shapes.split(";")]
+    else:
+        shapes = [(args.ppc, args.lb) if args.ppc else (ppc, -1)]
     subs = [cvx.Submap(sm.voxel_size, sm.trunc, wl.max_weight, 0, max_blocks=max_blocks, sets=4)
             for sm in wl.submaps]
-    scans, keep = [], []
-    for m, sm in enumerate(wl.submaps):
-        for sc in sm.scans:
-            p = torch.from_numpy(np.ascontiguousarray(sc.points)).cuda()
-            keep.append(p)
-            scans.append((m, p, sc.T_sub_sensor, None,
-                          cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range, sc.sensor,
-                                               sc.height, sc.width, ppc, lb)))
     handles = [s.handle for s in subs]
-    batch = _capi.cvx_batch_create(len(subs), len(scans))
-    for _ in range(args.profile_steps):
-        _capi.cvx_reset_submaps(handles)
-        _capi.cvx_integrate_batch(batch, handles, scans)
-    torch.cuda.synchronize()
-    assert _capi.cvx_batch_error(batch) == 0 and all(s.status() == 0 for s in subs)
-    c = [s.counters() for s in subs]
-    print(json.dumps({"profile_steps": args.profile_steps, "workload": wl.name, "submaps": len(subs),
-                      "scans": len(scans), "launch_shape": [ppc, lb],
-                      "input_points": sum(int(x[1].shape[0]) for x in scans),
-                      "counts": {k: sum(x[k] for x in c) for k in c[0]}}))
+    pts = [(m, torch.from_numpy(np.ascontiguousarray(sc.points)).cuda(), sc)
+           for m, sm in enumerate(wl.submaps) for sc in sm.scans]
+    batch = _capi.cvx_batch_create(len(subs), len(pts))
+    for ppc, lb in shapes:
+        scans = [(m, p, sc.T_sub_sensor, None,
+                  cvx.integrate_params(wl.weight_mode, wl.dropoff, wl.min_range, wl.max_range, sc.sensor,
+                                       sc.height, sc.width, ppc, lb)) for m, p, sc in pts]
+        for _ in range(args.profile_steps):
+            _capi.cvx_reset_submaps(handles)
+            _capi.cvx_integrate_batch(batch, handles, scans)
+        torch.cuda.synchronize()
+        assert _capi.cvx_batch_error(batch) == 0 and all(s.status() == 0 for s in subs)
+        c = [s.counters() for s in subs]
+        print(json.dumps({"profile_steps": args.profile_steps, "workload": wl.name, "submaps": len(subs),
+                          "scans": len(scans), "launch_shape": [ppc, lb],
+                          "input_points": sum(int(x[1].shape[0]) for x in scans),
+                          "counts": {k: sum(x[k] for x in c) for k in c[0]}}))
     _capi.cvx_batch_destroy(batch)
 
 
@@ -1169,6 +1187,10 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiler mode: run only the batched step of --workload this many times, eagerly "
                          "(--frames frames, or --scans LiDAR scans), no timing and no other forms")
+    ap.add_argument("--profile-shapes", default="",
+                    help="profiler mode: launch shapes 'ppc,lb;ppc,lb;...' run in turn, --profile-steps each")
+    ap.add_argument("--profile-kernel", default="batched", choices=["batched", "point_weights"],
+                    help="profiler mode: the batched step, or the learned form's weight kernel over --frames frames")
     args = ap.parse_args()
     if args.profile_steps > 0:
         return profile_steps(args)
