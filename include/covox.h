@@ -343,6 +343,15 @@ cvx_status cvx_integrate_batch(cvx_batch* batch, cvx_submap* const* maps, int32_
  * submaps in flight.  Results do not depend on it. */
 cvx_status cvx_batch_wave_limit(cvx_batch* batch, int32_t max_scans_per_wave);
 
+/* Tuning: the queue of a batched launch takes the submaps in groups of
+ * `group` consecutive submaps (by index in the launch's submap array): every
+ * scan of one group, round by round of equal frame rank, before the next
+ * group's (0 = all submaps in one group, the default).  Small groups keep a
+ * group's voxel fields and per-scan sums resident in the L2 between its
+ * scans when many large submaps share a launch; one group gives the most
+ * scans in flight.  Results do not depend on it. */
+cvx_status cvx_batch_submap_group(cvx_batch* batch, int32_t group);
+
 /* Tuning: each scan's merge runs as `parts` work items of the persistent
  * launch (1..256; 0 = chosen per round of the queue, a round being the scans
  * of equal rank in their submaps: the largest power of two in [8, 64] whose

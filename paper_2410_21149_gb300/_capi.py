@@ -118,6 +118,7 @@ SIGNATURES = {
     "cvx_batch_timing": (_i32, [_vp, _i32]),
     "cvx_batch_wave_limit": (_i32, [_vp, _i32]),
     "cvx_batch_merge_parts": (_i32, [_vp, _i32]),
+    "cvx_batch_submap_group": (_i32, [_vp, _i32]),
     "cvx_batch_test_missing_cta": (_i32, [_vp, _i32, _i64]),
     "cvx_batch_phase_times": (_i32, [_vp, _vp, _i32]),
     "cvx_point_features": (_i32, [_vp, _i32, _i32, _i32, ctypes.c_float, _vp, _vp]),
@@ -248,6 +249,10 @@ def cvx_batch_error(batch: int) -> int:
 
 def cvx_batch_wave_limit(batch: int, max_scans_per_wave: int) -> None:
     check(lib().cvx_batch_wave_limit(batch, int(max_scans_per_wave)), "cvx_batch_wave_limit")
+
+
+def cvx_batch_submap_group(batch: int, group: int) -> None:
+    check(lib().cvx_batch_submap_group(batch, int(group)), "cvx_batch_submap_group")
 
 
 def cvx_batch_merge_parts(batch: int, parts: int) -> None:

@@ -271,6 +271,7 @@ struct cvx_batch {
   int missing_cta;    // test hook (-1: off)
   long long polls;
   int merge_parts;    // merge items per scan (0: chosen per round of each launch)
+  int submap_group;   // queue order by groups of this many submaps (0: all submaps in one group)
 };
 
 namespace {
@@ -358,6 +359,12 @@ cvx_status cvx_batch_wave_limit(cvx_batch* b, int32_t max_scans_per_wave) {
   return CVX_OK;
 }
 
+cvx_status cvx_batch_submap_group(cvx_batch* b, int32_t group) {
+  if (!b || group < 0) return CVX_ERR_INVALID_ARG;
+  b->submap_group = group;
+  return CVX_OK;
+}
+
 cvx_status cvx_batch_merge_parts(cvx_batch* b, int32_t parts) {
   if (!b || parts < 0 || parts > kMaxMergeParts) return CVX_ERR_INVALID_ARG;
   b->merge_parts = parts;
@@ -421,16 +428,22 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     order.push_back(s);
   }
   if (order.empty()) return CVX_OK;
-  // queue order: rounds of scans of equal rank (cut into chunks of at most
-  // wave_limit scans); the merges of a round's scans follow in the next round
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return rank[a] < rank[c]; });
+  // queue order: groups of submap_group submaps one after another (all of
+  // them in one group by default), within a group rounds of scans of equal
+  // rank (cut into chunks of at most wave_limit scans); the merges of a
+  // round's scans follow in the next round
+  auto group_of = [&](int s) { return b->submap_group > 0 ? scans[s].submap / b->submap_group : 0; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return group_of(a) != group_of(c) ? group_of(a) < group_of(c) : rank[a] < rank[c];
+  });
   const int n_run = (int)order.size();
   std::vector<int> round_of(n_run);
   int n_rounds = 0;
   {
-    int prev = -1, in_round = 0;
+    long long prev = -1;
+    int in_round = 0;
     for (int k = 0; k < n_run; ++k) {
-      const int rk = rank[order[k]];
+      const long long rk = ((long long)group_of(order[k]) << 32) | (long long)rank[order[k]];
       if (rk != prev || (b->wave_limit > 0 && in_round >= b->wave_limit)) {
         ++n_rounds;
         in_round = 0;

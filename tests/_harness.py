@@ -125,7 +125,7 @@ def compare_colors(gpu, orc, c_tol, w_floor=1e-6, c_tol_w=0.0):
 
 
 def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=False, pipelined=False,
-                    wave_limit=0, point_weights=None, sets=0, colors=None, merge_parts=0, **over):
+                    wave_limit=0, point_weights=None, sets=0, colors=None, merge_parts=0, submap_group=0, **over):
     """Integrate all submaps of the workload with one cvx_integrate_batch call
     (scans of a submap are frames in order).  Returns the run_gpu tuple list."""
     import torch
@@ -158,6 +158,7 @@ def run_gpu_batched(wl: sg.Workload, storages=None, max_blocks=1 << 16, graph=Fa
     batch = _capi.cvx_batch_create(len(subs), len(scans))
     _capi.cvx_batch_wave_limit(batch, wave_limit)
     _capi.cvx_batch_merge_parts(batch, merge_parts)
+    _capi.cvx_batch_submap_group(batch, submap_group)
     handles = [s.handle for s in subs]
     if graph:
         s = torch.cuda.Stream()

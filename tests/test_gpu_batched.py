@@ -64,6 +64,30 @@ def test_merge_parts_do_not_change_results(mixed, parts):
     _capi.cvx_batch_destroy(b)
 
 
+@pytest.mark.parametrize("group,wave_limit", [(1, 0), (4, 0), (2, 3)])
+def test_submap_groups_do_not_change_results(mixed, group, wave_limit):
+    """The queue taking the submaps in groups of one, four or two (the last
+    with rounds cut into chunks of three scans): the same submaps as the
+    oracle's."""
+    storages = [m % 2 for m in range(len(mixed.submaps))]
+    g = run_gpu_batched(mixed, storages, sets=4, submap_group=group, wave_limit=wave_limit)
+    for m, (a, st) in enumerate(zip(g, storages)):
+        sm = mixed.submaps[m]
+        sub = sg.Workload(mixed.name, [sm], mixed.max_weight, mixed.weight_mode, mixed.dropoff,
+                          mixed.min_range, mixed.max_range, mixed.scene, st)
+        o = run_oracle(sub, fp16=bool(st))[0]
+        if st:
+            compare(a, o, 1e-3 * sm.trunc, fp16_trunc=sm.trunc)
+        else:
+            compare(a, o, 1e-5)
+        assert a[3]["frames"] == len(sm.scans)
+    from paper_2410_21149_gb300 import _capi
+    b = _capi.cvx_batch_create(1, 1)
+    with pytest.raises(_capi.CovoxError):
+        _capi.cvx_batch_submap_group(b, -1)
+    _capi.cvx_batch_destroy(b)
+
+
 def test_batched_equals_per_scan_path():
     wl = sg.make_c1(n_frames=4)
     wl2 = sg.make_c3(n_scans=4, scans_per_submap=2, rows=16, cols=256, n_boxes=300)
