@@ -53,6 +53,9 @@ struct ScanMeta {
   int lb;         // shared block slots
   int epoch_end;  // > 0: the submap's last scan of the launch, st->epoch advances by this much
   int parts;      // merge items of the scan
+  int rank;       // frame number of the scan within its submap in this launch
+  int part_chain; // 1: the previous scan's merge has the same parts, so merge part p waits only for
+                  // the previous merge's part p (the same spans, hence the same blocks)
 };
 
 struct BatchDev {
@@ -64,6 +67,7 @@ struct BatchDev {
   int n_segs;
   int n_scans;
   int* ctr;                 // head, err, exit count, scans closed, then per scan: tiles done, merge tickets, merged flag
+  int* part_done;           // [submaps of the launch][kMaxMergeParts]: 1 + rank of the last merge whose part p is done
   unsigned long long* phase_ns;   // [1 + 2 * n_scans]: launch start, per scan tiles done / merged
   long long polls;          // polls before a wait gives up
   int missing_cta;          // test hook: this CTA takes one item and leaves without doing it (-1: none)
@@ -160,8 +164,10 @@ __device__ void close_scan(const BatchDev& b, int s) {
   const ScanMeta& sm = b.meta[s];
   const SubmapDev& m = b.views[sm.view];
   State* st = m.st;
-  st->frames += 1;
-  st->sticky_err |= *((volatile int32_t*)m.frame_err);
+  // atomics: the close of the submap's next scan may run at the same time
+  // (its merge parts wait only for this merge's parts, not for this close)
+  atomicAdd(&st->frames, 1ull);
+  atomicOr(&st->sticky_err, *((volatile int32_t*)m.frame_err));
   *m.frame_err = 0;
   if (sm.epoch_end > 0) st->epoch += (uint32_t)sm.epoch_end;   // after the submap's last scan of the launch
   atomicAdd(b.ctr + 3, 1);
@@ -223,13 +229,19 @@ __global__ void __launch_bounds__(kTileThreads, COVOX_BATCHED_MIN_CTAS) batched_
         if (!wait_at_least(b, tiles_done(b, s), sm.n_tiles, &ok_smem)) continue;
         seen_tiles = s;
       }
-      if (sm.prev >= 0 && sm.prev != seen_merged) {
-        if (!wait_at_least(b, merged_flag(b, sm.prev), 1, &ok_smem)) continue;
-        seen_merged = sm.prev;
+      int* my_part = b.part_done + (size_t)(sm.view >> 2) * kMaxMergeParts + part;
+      if (sm.prev >= 0) {   // D and W in frame order
+        if (sm.part_chain) {
+          if (!wait_at_least(b, my_part, sm.rank, &ok_smem)) continue;
+        } else if (sm.prev != seen_merged) {
+          if (!wait_at_least(b, merged_flag(b, sm.prev), 1, &ok_smem)) continue;
+          seen_merged = sm.prev;
+        }
       }
       merge_part<(kVariant < 0)>(b, s, part, merge_smem(smem), red);
       if (threadIdx.x == 0) {
         __threadfence();
+        atomicExch(my_part, sm.rank + 1);   // this part's blocks are merged up to this scan
         if (atomicAdd(merge_ticket(b, s), 1) == sm.parts - 1) {
           close_scan(b, s);
           if (b.phase_ns) b.phase_ns[2 + 2 * s] = global_ns();
@@ -271,6 +283,7 @@ struct cvx_batch {
   int missing_cta;    // test hook (-1: off)
   long long polls;
   int merge_parts;    // merge items per scan (0: chosen per round of each launch)
+  int* part_done;     // [max_maps][kMaxMergeParts] per-part merge progress (device)
   int submap_group;   // queue order by groups of this many submaps (0: all submaps in one group)
 };
 
@@ -320,12 +333,14 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
   b->polls = kWaitPolls;
   if (cudaMalloc(&b->dev, L.total) != cudaSuccess || cudaMallocHost(&b->host, L.total) != cudaSuccess ||
       cudaMalloc((void**)&b->ctr, counter_bytes(max_scans)) != cudaSuccess ||
+      cudaMalloc((void**)&b->part_done, sizeof(int) * (size_t)max_submaps * kMaxMergeParts) != cudaSuccess ||
       cudaMalloc((void**)&b->phase_ns, sizeof(unsigned long long) * (1 + 2 * (size_t)max_scans)) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     if (b->dev) cudaFree(b->dev);
     if (b->host) cudaFreeHost(b->host);
     if (b->ctr) cudaFree(b->ctr);
+    if (b->part_done) cudaFree(b->part_done);
     if (b->phase_ns) cudaFree(b->phase_ns);
     delete b;
     return CVX_ERR_OOM;
@@ -348,6 +363,7 @@ void cvx_batch_destroy(cvx_batch* b) {
   cudaFree(b->dev);
   cudaFreeHost(b->host);
   cudaFree(b->ctr);
+  cudaFree(b->part_done);
   cudaFree(b->phase_ns);
   cudaEventDestroy(b->copied);
   delete b;
@@ -526,6 +542,10 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     return p;
   };
   for (int k = 0; k < n_run; ++k) hm[k].parts = parts_of_round(round_of[k]);
+  for (int k = 0; k < n_run; ++k) {
+    hm[k].rank = rank[order[k]];
+    hm[k].part_chain = hm[k].prev >= 0 && hm[hm[k].prev].parts == hm[k].parts;
+  }
   // queue segments, round by round: merges of the previous round's
   // single-set scans (their submaps' next tiles wait for them), this round's
   // tiles, then the merges of the previous round's two-set scans (the next
@@ -570,7 +590,8 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
     // a scan left pending by the pipelined per-scan path is merged first
     if (flush_pending(maps[q], st, false) != CVX_OK) return CVX_ERR_CUDA;
   }
-  if (cudaMemsetAsync(b->ctr, 0, counter_bytes(n_run), st) != cudaSuccess) {
+  if (cudaMemsetAsync(b->ctr, 0, counter_bytes(n_run), st) != cudaSuccess ||
+      cudaMemsetAsync(b->part_done, 0, sizeof(int) * (size_t)n_maps * kMaxMergeParts, st) != cudaSuccess) {
     cudaGetLastError();
     return CVX_ERR_CUDA;
   }
@@ -584,6 +605,7 @@ cvx_status cvx_integrate_batch(cvx_batch* b, cvx_submap* const* maps, int32_t n_
   bd.n_segs = n_segs;
   bd.n_scans = n_run;
   bd.ctr = b->ctr;
+  bd.part_done = b->part_done;
   bd.phase_ns = b->timing ? b->phase_ns : nullptr;
   bd.polls = b->polls;
   bd.missing_cta = b->missing_cta;
