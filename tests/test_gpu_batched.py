@@ -1,5 +1,6 @@
 """Batched persistent integration (many submaps, uneven mixed scans, one
-cooperative launch) against the CPU oracle and the per-scan path."""
+persistent launch working through a queue of tile and merge items) against
+the CPU oracle and the per-scan path."""
 import numpy as np
 import pytest
 
