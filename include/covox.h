@@ -325,9 +325,12 @@ cvx_status cvx_batch_create(int32_t max_submaps, int32_t max_scans, cvx_batch** 
  * as successive cvx_integrate_scan calls); scans of different submaps are
  * independent; empty scans are skipped.  The kernel takes tile and merge
  * work items from one queue in dependency order (a scan's tiles wait for the
- * merge that last used their per-scan set -- with pipelined submaps, two
- * sets, so consecutive scans overlap --, a scan's merge for its tiles and for
- * the previous scan's merge), so no grid-wide barrier is needed.  Asynchronous
+ * merge that last used their per-scan set -- with pipelined submaps two
+ * sets, with four-set submaps four, so consecutive scans overlap --, a
+ * scan's merge for its tiles and for the previous scan's merge: each merge
+ * part only for the same part of the previous merge when both have the same
+ * part count, since it covers the same blocks), so no grid-wide barrier is
+ * needed.  Asynchronous
  * on `stream`; the descriptor upload reads the batch object's pinned staging
  * buffer when the stream executes it, so a CUDA graph that captured this call
  * replays the staging buffer's contents at replay time: do not issue another
